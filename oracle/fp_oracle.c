@@ -1,0 +1,243 @@
+/*
+ * Plain CPU oracle for decoding dictionary-compressed string columns.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load or call this code.  It shares no
+ * source, header, table or helper with the CUDA decoder.
+ *
+ * What it computes (the plain definition the GPU decoder must reproduce):
+ *   - Decoding concatenates the tokens that the codes index, with no padding
+ *     between tokens (paper Sec. 1 and Sec. 2.1; Sec. 3 "tokens are
+ *     concatenated without padding").
+ *   - Codec formats (Sec. 2.1): OnPair-16 = 16-bit codes, OnPair-12 = 12-bit
+ *     codes, both into dictionaries of tokens of at most 16 bytes; FSST-8 =
+ *     byte codes into a 255-symbol table of tokens of at most 8 bytes, where
+ *     the reserved escape code 255 is followed by one literal byte.
+ *   - Output (Sec. 5): a variable-length string array: byte-packed string
+ *     data plus an array of fixed-width offsets (uint32 here).
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - 12-bit codes are stored as an LSB-first bitstream: code i occupies
+ *     stream bits [12i, 12i+12), stream bit b is bit (b mod 8) of byte b/8.
+ *   - OnPair-16 codes are little-endian 16-bit words.
+ *   - code_offsets index code *slots*; for FSST-8 a literal byte is a slot.
+ *   - An escape in the last slot of a string (no literal follows) and a code
+ *     >= n_entries are corrupt input.  A corrupt code contributes no bytes.
+ *   - out_offsets[0] = 0 even when code_offsets[0] != 0.
+ *
+ * Every loop is the definition written out: the 12-bit reader goes bit by
+ * bit, token copies go byte by byte, and nothing is over-copied.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+enum { FPO_ONPAIR16 = 1, FPO_ONPAIR12 = 2, FPO_FSST8 = 3 };
+enum { FPO_OK = 0, FPO_ERR_ARG = 1, FPO_ERR_CORRUPT = 4, FPO_ERR_CAPACITY = 5,
+       FPO_ERR_OVERFLOW = 6 };
+/* error kinds reported as a bit set */
+enum { FPO_BIT_CORRUPT = 1, FPO_BIT_CAPACITY = 2, FPO_BIT_OVERFLOW = 4 };
+
+static int code_bits(int codec) {
+    return codec == FPO_ONPAIR16 ? 16 : codec == FPO_ONPAIR12 ? 12 : codec == FPO_FSST8 ? 8 : 0;
+}
+
+/* Read stream bit b (LSB-first within each byte). */
+static unsigned read_bit(const uint8_t* stream, uint64_t b) {
+    return (stream[b / 8] >> (b % 8)) & 1u;
+}
+
+/* Code in slot s of a stored stream. */
+static uint32_t read_code(int codec, const uint8_t* stream, uint64_t s) {
+    if (codec == FPO_ONPAIR16) {
+        return (uint32_t)stream[2 * s] | ((uint32_t)stream[2 * s + 1] << 8);
+    }
+    if (codec == FPO_ONPAIR12) {
+        uint32_t c = 0;
+        for (unsigned k = 0; k < 12; ++k) c |= read_bit(stream, 12 * s + k) << k;
+        return c;
+    }
+    return stream[s];
+}
+
+/* Unpack n 12-bit codes, bit by bit. */
+void fpo_unpack12(const uint8_t* stream, uint64_t n, uint16_t* out) {
+    for (uint64_t i = 0; i < n; ++i) out[i] = (uint16_t)read_code(FPO_ONPAIR12, stream, i);
+}
+
+typedef struct {
+    int codec;
+    const uint8_t* dict_bytes;
+    const uint32_t* dict_offsets;
+    uint32_t n_entries;
+    const uint8_t* stream;
+    uint64_t n_slots;          /* whole code slots present in the stream */
+    const uint32_t* code_offsets;
+} column_t;
+
+/*
+ * Decode strings [s0, s1) into out (whose byte 0 corresponds to output
+ * position base).  When out is NULL only the sizes are computed.  Writes
+ * relative string ends into ends[i - s0] (may be NULL).  Returns the number
+ * of bytes produced and ORs error bits into *err.  Bytes beyond `cap`
+ * (absolute) are not written.
+ */
+static uint64_t decode_range(const column_t* c, uint32_t s0, uint32_t s1, uint8_t* out,
+                             uint64_t base, uint64_t cap, uint64_t* ends, unsigned* err) {
+    uint64_t pos = base;
+    for (uint32_t i = s0; i < s1; ++i) {
+        uint64_t j = c->code_offsets[i], end = c->code_offsets[i + 1];
+        while (j < end) {
+            uint32_t code = read_code(c->codec, c->stream, j);
+            if (c->codec == FPO_FSST8 && code == 255) {
+                if (j + 1 >= end) { *err |= FPO_BIT_CORRUPT; j += 1; continue; }
+                uint8_t lit = (uint8_t)read_code(c->codec, c->stream, j + 1);
+                if (out && pos < cap) out[pos - base] = lit;
+                pos += 1;
+                j += 2;
+                continue;
+            }
+            if (code >= c->n_entries) { *err |= FPO_BIT_CORRUPT; j += 1; continue; }
+            for (uint32_t b = c->dict_offsets[code]; b < c->dict_offsets[code + 1]; ++b) {
+                if (out && pos < cap) out[pos - base] = c->dict_bytes[b];
+                pos += 1;
+            }
+            j += 1;
+        }
+        if (ends) ends[i - s0] = pos;
+    }
+    return pos - base;
+}
+
+static int check_column(const column_t* c, uint32_t n_strings, unsigned* err) {
+    int w = code_bits(c->codec);
+    if (!w) return FPO_ERR_ARG;
+    uint32_t max_len = c->codec == FPO_FSST8 ? 8 : 16;
+    uint32_t max_entries = c->codec == FPO_ONPAIR16 ? 65536u : c->codec == FPO_ONPAIR12 ? 4096u : 255u;
+    if (c->n_entries == 0 || c->n_entries > max_entries) return FPO_ERR_ARG;
+    for (uint32_t e = 0; e < c->n_entries; ++e) {
+        uint32_t L = c->dict_offsets[e + 1] - c->dict_offsets[e];
+        if (c->dict_offsets[e + 1] < c->dict_offsets[e] || L < 1 || L > max_len) return FPO_ERR_ARG;
+    }
+    for (uint32_t i = 0; i < n_strings; ++i)
+        if (c->code_offsets[i] > c->code_offsets[i + 1]) { *err |= FPO_BIT_CORRUPT; return FPO_ERR_CORRUPT; }
+    if (c->code_offsets[n_strings] > c->n_slots) { *err |= FPO_BIT_CORRUPT; return FPO_ERR_CORRUPT; }
+    return FPO_OK;
+}
+
+static int status_of(unsigned err) {
+    if (err & FPO_BIT_CORRUPT) return FPO_ERR_CORRUPT;
+    if (err & FPO_BIT_CAPACITY) return FPO_ERR_CAPACITY;
+    if (err & FPO_BIT_OVERFLOW) return FPO_ERR_OVERFLOW;
+    return FPO_OK;
+}
+
+/*
+ * Decode a whole column.  out_offsets has n_strings + 1 entries.  Returns a
+ * status (FPO_*); *err_bits receives the set of error kinds seen and
+ * *total the decoded size (also when it exceeds the capacity).
+ */
+int fpo_decode(int codec, const uint8_t* dict_bytes, const uint32_t* dict_offsets, uint32_t n_entries,
+               const uint8_t* stream, uint64_t stream_bytes, const uint32_t* code_offsets,
+               uint32_t n_strings, uint8_t* out, uint64_t out_capacity, uint32_t* out_offsets,
+               uint64_t* total, unsigned* err_bits) {
+    column_t c = {codec, dict_bytes, dict_offsets, n_entries, stream,
+                  code_bits(codec) ? stream_bytes * 8 / (uint64_t)code_bits(codec) : 0, code_offsets};
+    unsigned err = 0;
+    int st = check_column(&c, n_strings, &err);
+    if (err_bits) *err_bits = err;
+    if (st != FPO_OK) return st;
+    uint64_t* ends = (uint64_t*)malloc(sizeof(uint64_t) * (n_strings ? n_strings : 1));
+    if (!ends) return FPO_ERR_ARG;
+    uint64_t D = decode_range(&c, 0, n_strings, out, 0, out ? out_capacity : 0, ends, &err);
+    if (out_offsets) {
+        out_offsets[0] = 0;
+        for (uint32_t i = 0; i < n_strings; ++i) out_offsets[i + 1] = (uint32_t)ends[i];
+    }
+    free(ends);
+    if (out && D > out_capacity) err |= FPO_BIT_CAPACITY;
+    if (D > 0x7fffffffull) err |= FPO_BIT_OVERFLOW;
+    if (total) *total = D;
+    if (err_bits) *err_bits = err;
+    return status_of(err);
+}
+
+/* ---- the same decode spread over threads, for the CPU baseline timing ---- */
+
+typedef struct {
+    const column_t* c;
+    uint32_t s0, s1;
+    uint8_t* out;
+    uint64_t base, cap;
+    uint64_t* ends;
+    uint64_t size;
+    unsigned err;
+    int sizes_only;
+} job_t;
+
+static void* run_job(void* p) {
+    job_t* j = (job_t*)p;
+    if (j->sizes_only) {
+        j->size = decode_range(j->c, j->s0, j->s1, NULL, 0, 0, NULL, &j->err);
+    } else {
+        decode_range(j->c, j->s0, j->s1, j->out + j->base, j->base, j->cap, j->ends, &j->err);
+    }
+    return NULL;
+}
+
+/*
+ * Thread-parallel decode: each thread takes a contiguous string range; a
+ * first pass sizes each range, a serial prefix places them, a second pass
+ * decodes in place.  Same result as fpo_decode.
+ */
+int fpo_decode_mt(int codec, const uint8_t* dict_bytes, const uint32_t* dict_offsets, uint32_t n_entries,
+                  const uint8_t* stream, uint64_t stream_bytes, const uint32_t* code_offsets,
+                  uint32_t n_strings, uint8_t* out, uint64_t out_capacity, uint32_t* out_offsets,
+                  uint64_t* total, unsigned* err_bits, int n_threads) {
+    column_t c = {codec, dict_bytes, dict_offsets, n_entries, stream,
+                  code_bits(codec) ? stream_bytes * 8 / (uint64_t)code_bits(codec) : 0, code_offsets};
+    unsigned err = 0;
+    int st = check_column(&c, n_strings, &err);
+    if (err_bits) *err_bits = err;
+    if (st != FPO_OK) return st;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    job_t jobs[256];
+    pthread_t th[256];
+    uint64_t* ends = (uint64_t*)malloc(sizeof(uint64_t) * (n_strings ? n_strings : 1));
+    if (!ends) return FPO_ERR_ARG;
+    for (int t = 0; t < n_threads; ++t) {
+        uint32_t s0 = (uint32_t)((uint64_t)n_strings * t / n_threads);
+        uint32_t s1 = (uint32_t)((uint64_t)n_strings * (t + 1) / n_threads);
+        job_t jb = {&c, s0, s1, out, 0, 0, ends + s0, 0, 0, 1};
+        jobs[t] = jb;
+    }
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, run_job, &jobs[t]);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    uint64_t base = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t].base = base;
+        base += jobs[t].size;
+        err |= jobs[t].err;
+        jobs[t].err = 0;
+        jobs[t].sizes_only = 0;
+        jobs[t].cap = out_capacity;
+    }
+    uint64_t D = base;
+    if (out && D <= out_capacity) {
+        for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, run_job, &jobs[t]);
+        for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+        if (out_offsets) {
+            out_offsets[0] = 0;
+            for (uint32_t i = 0; i < n_strings; ++i) out_offsets[i + 1] = (uint32_t)ends[i];
+        }
+    } else if (out) {
+        err |= FPO_BIT_CAPACITY;
+    }
+    free(ends);
+    if (D > 0x7fffffffull) err |= FPO_BIT_OVERFLOW;
+    if (total) *total = D;
+    if (err_bits) *err_bits = err;
+    return status_of(err);
+}
