@@ -1,0 +1,387 @@
+"""Benchmark: decode throughput of a dictionary-compressed string column on
+GB300, through the C ABI (libfastpair.so).
+
+One step = one decode of the whole column (code unpack, length scan with
+look-back, assembly, string offsets) with inputs resident in HBM.  Prints one
+JSON line.  ``--impl reference`` times the CPU oracle instead (on the host
+cores, bounded sample of the same workload).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (codec, n_strings, description)
+    "onpair12_10m": (synth.ONPAIR12, 10_000_000,
+                     "OnPair-12, 4,096-entry log-token dictionary, 10M strings of 20-200 B, Zipf(1.2)"),
+    "fsst8_16m": (synth.FSST8, 16_000_000,
+                  "FSST-8 with escapes, 255 URL/identifier symbols, 16M lognormal strings (median 40 B)"),
+    "onpair16_100k": (synth.ONPAIR16, 100_000,
+                      "OnPair-16, 65,536-entry dictionary, 100k strings of 1-40 codes, Zipf(1.1)"),
+}
+METRIC = "decoded GB/s (single-column decode, inputs resident in HBM)"
+L2_BYTES = 126 * 1024 * 1024
+
+
+def env_rank():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def algorithmic_bytes(col, total: int, codec: int) -> int:
+    """Bytes a decode must move at least: the code slots it reads, the string
+    offsets it reads and writes, the output it writes, the dictionary once."""
+    co = col.code_offsets
+    used_slots = int(co[-1]) - int(co[0])
+    code_bytes = (used_slots * synth.CODE_BITS[codec] + 7) // 8
+    n = col.n_strings
+    dict_bytes = col.dictionary.n_entries * (synth.MAX_TOKEN[codec] + 1)
+    return code_bytes + 4 * (n + 1) + total + 4 * (n + 1) + dict_bytes
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the library build that is running now."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        from paper_2609_15034_gb300 import _build
+        digest = _build._inputs_digest()
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("source_digest") == digest:
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(col, target_s: float, threads: int):
+    """Time the oracle (as it stands) on a bounded prefix of the column."""
+    import oracle
+    n = col.n_strings
+    # size the sample from a short probe
+    probe_n = min(n, 20000)
+    co = col.code_offsets
+    t0 = time.perf_counter()
+    r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, co[:probe_n + 1],
+                      threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    rate = r.total / dt
+    want_bytes = rate * target_s
+    per_string = max(r.total / max(probe_n, 1), 1.0)
+    m = int(min(n, max(probe_n, want_bytes / per_string)))
+    t0 = time.perf_counter()
+    r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, co[:m + 1],
+                      threads=threads)
+    dt = time.perf_counter() - t0
+    return r.total / dt / 1e9, m, r.total, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    codec, n, desc = WORKLOADS[args.workload]
+    col = synth.column(codec, 0, n)
+    threads = os.cpu_count() or 1
+    vals, samples = [], []
+    per_step = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
+    for i in range(args.warmup + args.steps):
+        gbs, m, total, dt = cpu_oracle_rate(col, per_step, threads)
+        if i >= args.warmup:
+            vals.append(gbs)
+            samples.append((m, total, dt))
+    value = statistics.mean(vals)
+    m, total, dt = samples[-1]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc, "n_strings": n},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {m} of {n} strings ({total} decoded bytes) per step"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2609_15034_gb300 as fp
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    codec, n, desc = WORKLOADS[args.workload]
+    if args.n_strings:
+        n = args.n_strings
+    col = synth.column(codec, rank, n)   # one independent replica column per rank
+    fp.variant_select(codec, args.variant)
+
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    d = fp.Dict(codec, col.dictionary.data, col.dictionary.offsets, sh)
+    codes = torch.from_numpy(col.stream).to(dev)
+    co = torch.from_numpy(col.code_offsets.view(np.int32)).to(dev)
+    st, total = fp.decoded_size_tensors(codec, d, codes, co, n, sh)
+    if st != fp.OK:
+        raise RuntimeError(f"decoded_size: {fp.STATUS_NAMES[st]} {fp.last_error()}")
+    out = torch.empty(total, dtype=torch.uint8, device=dev)
+    offs = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    codes_bytes = codes.numel()
+
+    def step():
+        fp.decode(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
+                  offs.data_ptr(), sh)
+
+    # correctness gate on a sample before timing (the full oracle check lives in the tests)
+    step()
+    if fp.sync_status(sh) != fp.OK:
+        raise RuntimeError(fp.last_error())
+
+    gpu_id = "0"
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = str(local_rank)
+    sampler = ClockSampler(gpu_id)
+    # settle clocks (untimed), then the warm-up steps
+    t_end = time.time() + args.settle
+    while time.time() < t_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    st = fp.sync_status(sh)
+    if st != fp.OK:
+        raise RuntimeError(fp.last_error())
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        bt = torch.tensor([float(total)], device=dev, dtype=torch.float64)
+        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+        all_bytes = float(bt.item())
+    else:
+        all_bytes = float(total)
+
+    value = all_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    alg = algorithmic_bytes(col, total, codec)
+    peak, peak_kind = load_peaks()
+    achieved = alg / avg_launch_s / 1e9
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # plain one-thread-per-string GPU decode, same column, same clock
+        plain_ms = []
+        for i in range(3 + args.plain_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fp.decode_plain(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
+                            offs.data_ptr(), sh)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                plain_ms.append(a.elapsed_time(b))
+        if fp.sync_status(sh) != fp.OK:
+            raise RuntimeError(fp.last_error())
+        plain_gbs = total / (statistics.mean(plain_ms) * 1e-3) / 1e9
+        extra["plain_gpu"] = {"value": round(plain_gbs, 2), "unit": "GB/s", "kind": "one thread per string",
+                              "ms": round(statistics.mean(plain_ms), 3)}
+
+        # end to end through the public API with host buffers (pinned)
+        h_codes = torch.from_numpy(col.stream).pin_memory()
+        h_co = torch.from_numpy(col.code_offsets.view(np.int32)).pin_memory()
+        h_out = torch.empty(total, dtype=torch.uint8).pin_memory()
+        h_offs = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+        d_codes = torch.empty_like(codes)
+        d_co = torch.empty_like(co)
+
+        def e2e_step():
+            d_codes.copy_(h_codes, non_blocking=True)
+            d_co.copy_(h_co, non_blocking=True)
+            fp.decode(codec, d, d_codes.data_ptr(), codes_bytes, d_co.data_ptr(), n, out.data_ptr(), total,
+                      offs.data_ptr(), sh)
+            h_out.copy_(out, non_blocking=True)
+            h_offs.copy_(offs, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_n = max(3, min(args.steps, 20))
+        a.record(stream)
+        for _ in range(e2e_n):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if fp.sync_status(sh) != fp.OK:
+            raise RuntimeError(fp.last_error())
+        e2e_s = a.elapsed_time(b) * 1e-3 / e2e_n
+        extra["e2e"] = {"value": round(total / e2e_s / 1e9, 3), "unit": "GB/s",
+                        "h2d_bytes_per_step": int(h_codes.numel() + h_co.numel() * 4),
+                        "d2h_bytes_per_step": int(total + (n + 1) * 4)}
+        # spot-check the host copy against the device result
+        if not torch.equal(h_out[:4096], out[:4096].cpu()):
+            raise RuntimeError("end-to-end output mismatch")
+
+        # CPU oracle on the host cores (reported baseline, not a target)
+        threads = os.cpu_count() or 1
+        gbs, m, tb, dt = cpu_oracle_rate(col, args.cpu_seconds, threads)
+        extra["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                                 "sample": f"first {m} of {n} strings ({tb} decoded bytes), {dt:.1f} s"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    var = fp.variant_selected(codec)
+    vinfo = fp.variant_info(codec, var)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc, "n_strings": n, "decoded_bytes": int(total),
+                   "code_bytes": int(codes_bytes), "mean_bytes_per_code": round(total / max(col.n_slots, 1), 3),
+                   "l2": "inputs and output larger than L2 (no flush needed)" if total + codes_bytes > L2_BYTES
+                   else "inputs L2-resident (small workload)",
+                   "variant": vinfo, "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": load_traffic(args.workload), "algorithmic_bytes_per_launch": alg,
+                     "kernel_ms": round(avg_launch_s * 1e3, 4)},
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+    }
+    line.update(extra)
+    if "e2e" not in line:
+        line["e2e"] = None
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="onpair12_10m", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed decoding before warm-up")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
+    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--quick", action="store_true", help="skip the baselines and the e2e leg")
+    ap.add_argument("--variant", type=int, default=-1, help="decode variant (-1: built-in default)")
+    ap.add_argument("--n-strings", type=int, default=0, help="override the workload's string count")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, world, local_rank = env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

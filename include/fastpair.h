@@ -1,0 +1,197 @@
+/*
+ * fastpair.h -- C ABI of the GB300 decoder for dictionary-compressed string
+ * columns (FSST-family codecs, FastPair, arXiv 2609.15034).
+ *
+ * The problem (paper Sec. 1, Sec. 2.1): a column of strings is stored as a
+ * stream of fixed-width codes; each code indexes a token of a trained
+ * dictionary, and a string decodes to the concatenation of its codes'
+ * tokens, with no padding between tokens.  The output (paper Sec. 5) is a
+ * variable-length string array: byte-packed string data plus an array of
+ * fixed-width offsets.
+ *
+ * Codecs (paper Sec. 2.1):
+ *   FP_ONPAIR16  16-bit codes, up to 65,536 tokens of 1..16 bytes.
+ *   FP_ONPAIR12  12-bit codes, up to 4,096 tokens of 1..16 bytes.
+ *   FP_FSST8     8-bit codes, up to 255 tokens of 1..8 bytes; code 255 is the
+ *                escape: the slot after it holds one literal byte.
+ *
+ * Stored layouts:
+ *   - OnPair-16: little-endian uint16 per code.
+ *   - OnPair-12: LSB-first bitstream; code i occupies stream bits
+ *     [12 i, 12 i + 12), stream bit b is bit (b mod 8) of byte b / 8.
+ *   - FSST-8: one byte per slot (codes and the literal bytes after escapes).
+ *   A "slot" is one code position (for FSST-8 a literal byte is a slot too).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device pointers owned by the caller; the library
+ *     never frees them.  Pointers named h_* are host pointers.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are stream-ordered and asynchronous unless stated otherwise.
+ *   - Host-detectable argument errors return at once and launch nothing.
+ *     Errors found in the data on the device (see fp_sync_status) are
+ *     recorded in a sticky per-stream status word and never trap; on a data
+ *     error the output contents are unspecified, but every write stays
+ *     inside [d_out_bytes, d_out_bytes + out_capacity) and d_out_offsets.
+ *   - fp_last_error() returns a thread-local text for the last failure.
+ *
+ * This header declares only what libfastpair.so exports.
+ */
+#ifndef FASTPAIR_H
+#define FASTPAIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fp_stream_t; /* same type as cudaStream_t */
+
+typedef enum fp_codec {
+    FP_ONPAIR16 = 1,
+    FP_ONPAIR12 = 2,
+    FP_FSST8 = 3
+} fp_codec;
+
+typedef enum fp_status {
+    FP_OK = 0,
+    FP_ERR_ARG = 1,       /* invalid argument (host-detected)                */
+    FP_ERR_CUDA = 2,      /* a CUDA runtime call failed                      */
+    FP_ERR_NOMEM = 3,     /* device or host allocation failed                */
+    FP_ERR_CORRUPT = 4,   /* code >= n_entries, escape in a string's last     */
+                          /* slot, code_offsets not monotone or past the      */
+                          /* end of the code buffer                           */
+    FP_ERR_CAPACITY = 5,  /* decoded size exceeds out_capacity                */
+    FP_ERR_OVERFLOW = 6,  /* decoded size exceeds 2^31 - 1 (int32 offsets)    */
+    FP_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up               */
+    FP_ERR_BUSY = 8,      /* resource busy / budget exhausted                 */
+    FP_ERR_NOT_READY = 9  /* result not available yet                         */
+} fp_status;
+
+/* Opaque, library-owned, device-resident dictionary. */
+typedef struct fp_dict fp_dict;
+
+/*
+ * fp_dict_upload -- validate a dictionary and make it device-resident.
+ *
+ * Paper Sec. 1 and Sec. 3.2: the decoder reads fixed-size dictionary
+ * entries addressed directly by the code, plus a separate table of token
+ * lengths.  This call repacks the interchange form (token i is
+ * h_bytes[h_offsets[i] .. h_offsets[i+1])) into that device layout.
+ *
+ *   codec       one of fp_codec.
+ *   h_bytes     host, concatenated token bytes (may be NULL only if every
+ *               token is empty, which is itself invalid).
+ *   h_offsets   host, n_entries + 1 non-decreasing uint32 offsets.
+ *   n_entries   1..65,536 (OnPair-16), 1..4,096 (OnPair-12), 1..255 (FSST-8).
+ *   stream      stream for the uploads; the call synchronises it before it
+ *               returns (the host buffers may be reused at once).
+ *   out         receives the dictionary handle.
+ *
+ * Errors: FP_ERR_ARG if a token length is outside 1..16 (OnPair) or 1..8
+ * (FSST-8), n_entries is out of range or a pointer is NULL; FP_ERR_NOMEM;
+ * FP_ERR_CUDA.  Duplicate tokens are allowed.
+ */
+fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t* h_offsets,
+                         uint32_t n_entries, fp_stream_t stream, fp_dict** out);
+
+/* Release a dictionary (synchronises the device first).  NULL is a no-op. */
+fp_status fp_dict_free(fp_dict* dict);
+
+/*
+ * fp_decode -- decode one column into Arrow-style bytes plus offsets.
+ *
+ * Paper Sec. 2.1 and Sec. 3 (Algorithm 1): for every string i, the output
+ * bytes d_out_bytes[d_out_offsets[i] .. d_out_offsets[i+1]) are the
+ * concatenation of the tokens of the codes in slots
+ * [d_code_offsets[i], d_code_offsets[i+1]); for FSST-8 an escape (255)
+ * contributes the literal byte in the slot after it.  Output positions come
+ * from a prefix sum of token lengths computed on the device in the same
+ * launch (the paper stores them as a precomputed sidecar, Sec. 3.1).
+ *
+ *   codec           must equal the dictionary's codec.
+ *   dict            from fp_dict_upload, on the current device.
+ *   d_codes         device, stored code buffer, 16-byte aligned.
+ *   codes_bytes     size of the code buffer in bytes; only whole slots in it
+ *                   are read.
+ *   d_code_offsets  device, n_strings + 1 uint32 slot indices, non-decreasing;
+ *                   d_code_offsets[0] may be non-zero (a slice of a larger
+ *                   stream).  Slots before it and after d_code_offsets[n]
+ *                   are never decoded.
+ *   n_strings       number of strings (0 allowed).
+ *   d_out_bytes     device, 16-byte aligned, out_capacity bytes.
+ *   out_capacity    bytes available at d_out_bytes.
+ *   d_out_offsets   device, n_strings + 1 uint32; d_out_offsets[0] = 0.
+ *   stream          launch stream.
+ *
+ * Returns FP_OK once the launch is enqueued, or a host-detected error
+ * (FP_ERR_ARG, FP_ERR_NOMEM, FP_ERR_CUDA).  Data errors are reported by
+ * fp_sync_status.  Calls on one stream share a library-owned workspace and
+ * must not overlap; calls on different streams may run concurrently.
+ * The first call on a stream allocates its workspace (call it once before
+ * capturing the stream into a CUDA graph).
+ */
+fp_status fp_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                    const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                    uint64_t out_capacity, uint32_t* d_out_offsets, fp_stream_t stream);
+
+/*
+ * fp_decoded_size -- decoded size of a column, synchronously.
+ *
+ * Same inputs and meaning as fp_decode; runs the length pass only and
+ * synchronises `stream`.  *h_total receives the decoded size in bytes.
+ * Returns the column's data status (FP_ERR_CORRUPT, FP_ERR_OVERFLOW, ...)
+ * as fp_sync_status would.
+ */
+fp_status fp_decoded_size(fp_codec codec, const fp_dict* dict, const void* d_codes,
+                          uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                          fp_stream_t stream, uint64_t* h_total);
+
+/*
+ * fp_decode_plain -- baseline decoder with one thread per string.
+ *
+ * Same arguments, result and error behaviour as fp_decode.  Each thread
+ * walks its string's codes serially and copies token bytes one at a time
+ * from the dictionary in its interchange layout (offset table, then bytes),
+ * after a separate per-string length pass and prefix sum.  It exists to be
+ * timed beside fp_decode.
+ */
+fp_status fp_decode_plain(fp_codec codec, const fp_dict* dict, const void* d_codes,
+                          uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                          uint8_t* d_out_bytes, uint64_t out_capacity, uint32_t* d_out_offsets,
+                          fp_stream_t stream);
+
+/*
+ * fp_sync_status -- synchronise `stream`, then read and clear its sticky
+ * data-error status.  Returns FP_OK or, by priority, FP_ERR_TIMEOUT,
+ * FP_ERR_CORRUPT, FP_ERR_CAPACITY, FP_ERR_OVERFLOW; FP_ERR_CUDA if the
+ * synchronisation itself failed.
+ */
+fp_status fp_sync_status(fp_stream_t stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* fp_last_error(void);
+
+/*
+ * Decode variants (tile shapes).  A variant fixes the threads per block, the
+ * code slots each thread decodes and where the dictionary is read from
+ * (shared memory staged once per block, or the L1/L2 cache path).
+ *
+ * fp_variant_count  number of compiled variants for a codec.
+ * fp_variant_info   describe variant v: threads, slots per thread, 1 if the
+ *                   dictionary is staged in shared memory.
+ * fp_variant_select make variant v the one fp_decode uses for the codec in
+ *                   this process (v = -1 restores the built-in default).
+ * fp_variant_selected  the variant fp_decode currently uses for the codec.
+ */
+int fp_variant_count(fp_codec codec);
+fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* slots_per_thread,
+                          uint32_t* dict_in_smem);
+fp_status fp_variant_select(fp_codec codec, int v);
+int fp_variant_selected(fp_codec codec);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTPAIR_H */

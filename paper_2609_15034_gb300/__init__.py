@@ -1,0 +1,186 @@
+"""Python binding of libfastpair.so (C ABI in include/fastpair.h).
+
+Argument marshalling only: every step of decoding runs in the library's
+CUDA kernels.  The library is compiled in-tree for sm_103a by
+:mod:`paper_2609_15034_gb300._build`; if it cannot be built or loaded,
+every call raises -- there is no CPU fallback.
+
+Functions keep the C names without the ``fp_`` prefix.  Device buffers are
+passed as integer addresses (``tensor.data_ptr()``) or as torch tensors via
+the ``*_tensors`` helpers; streams as ``cudaStream_t`` integers
+(``torch.cuda.current_stream().cuda_stream``) or ``None`` for the default
+stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+ONPAIR16, ONPAIR12, FSST8 = 1, 2, 3
+CODEC_IDS = {"onpair16": ONPAIR16, "onpair12": ONPAIR12, "fsst8": FSST8}
+CODE_BITS = {ONPAIR16: 16, ONPAIR12: 12, FSST8: 8}
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_CORRUPT, ERR_CAPACITY, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, \
+    ERR_NOT_READY = range(10)
+STATUS_NAMES = {0: "FP_OK", 1: "FP_ERR_ARG", 2: "FP_ERR_CUDA", 3: "FP_ERR_NOMEM", 4: "FP_ERR_CORRUPT",
+                5: "FP_ERR_CAPACITY", 6: "FP_ERR_OVERFLOW", 7: "FP_ERR_TIMEOUT", 8: "FP_ERR_BUSY",
+                9: "FP_ERR_NOT_READY"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FastPairError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    from . import _build
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfastpair.so (building it first if its sources changed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            P, U32, U64, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+            L.fp_dict_upload.argtypes = [I, P, P, U32, P, ctypes.POINTER(P)]
+            L.fp_dict_free.argtypes = [P]
+            L.fp_decode.argtypes = [I, P, P, U64, P, U32, P, U64, P, P]
+            L.fp_decode_plain.argtypes = [I, P, P, U64, P, U32, P, U64, P, P]
+            L.fp_decoded_size.argtypes = [I, P, P, U64, P, U32, P, ctypes.POINTER(U64)]
+            L.fp_sync_status.argtypes = [P]
+            L.fp_last_error.restype = ctypes.c_char_p
+            L.fp_variant_count.argtypes = [I]
+            L.fp_variant_info.argtypes = [I, I, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32)]
+            L.fp_variant_select.argtypes = [I, I]
+            L.fp_variant_selected.argtypes = [I]
+            for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
+                         "fp_sync_status", "fp_variant_info", "fp_variant_select"):
+                getattr(L, name).restype = I
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().fp_last_error().decode()
+
+
+def _check(st: int, where: str) -> int:
+    if st != OK:
+        raise FastPairError(st, where, last_error())
+    return st
+
+
+def _stream(s) -> ctypes.c_void_p:
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    return ctypes.c_void_p(int(s))
+
+
+class Dict:
+    """A device-resident dictionary (fp_dict*)."""
+
+    def __init__(self, codec: int, data: np.ndarray, offsets: np.ndarray, stream=None):
+        data = np.ascontiguousarray(data, np.uint8)
+        offsets = np.ascontiguousarray(offsets, np.uint32)
+        if data.size == 0:
+            data = np.zeros(1, np.uint8)
+        h = ctypes.c_void_p()
+        _check(lib().fp_dict_upload(codec, data.ctypes.data, offsets.ctypes.data, offsets.size - 1,
+                                    _stream(stream), ctypes.byref(h)), "fp_dict_upload")
+        self.codec = codec
+        self.n_entries = offsets.size - 1
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise ValueError("dictionary was freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            _lib.fp_dict_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dict_upload(codec: int, data, offsets, stream=None) -> Dict:
+    return Dict(codec, data, offsets, stream)
+
+
+def decode(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+           out_ptr: int, capacity: int, out_offsets_ptr: int, stream=None, check: bool = True) -> int:
+    st = lib().fp_decode(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr,
+                         capacity, out_offsets_ptr, _stream(stream))
+    return _check(st, "fp_decode") if check else st
+
+
+def decode_plain(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                 out_ptr: int, capacity: int, out_offsets_ptr: int, stream=None, check: bool = True) -> int:
+    st = lib().fp_decode_plain(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr,
+                               capacity, out_offsets_ptr, _stream(stream))
+    return _check(st, "fp_decode_plain") if check else st
+
+
+def decoded_size(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                 stream=None) -> tuple[int, int]:
+    """Returns (status, total bytes)."""
+    tot = ctypes.c_uint64(0)
+    st = lib().fp_decoded_size(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings,
+                               _stream(stream), ctypes.byref(tot))
+    return st, int(tot.value)
+
+
+def sync_status(stream=None) -> int:
+    return lib().fp_sync_status(_stream(stream))
+
+
+def variant_count(codec: int) -> int:
+    return lib().fp_variant_count(codec)
+
+
+def variant_info(codec: int, v: int) -> dict:
+    t, k, s = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().fp_variant_info(codec, v, ctypes.byref(t), ctypes.byref(k), ctypes.byref(s)), "fp_variant_info")
+    return {"threads": t.value, "slots_per_thread": k.value, "dict_in_smem": bool(s.value)}
+
+
+def variant_select(codec: int, v: int) -> None:
+    _check(lib().fp_variant_select(codec, v), "fp_variant_select")
+
+
+def variant_selected(codec: int) -> int:
+    return lib().fp_variant_selected(codec)
+
+
+# ---- torch conveniences (tensors are only carriers of device memory) -------
+
+def decode_tensors(codec, d: Dict, codes, code_offsets, n_strings: int, out, out_offsets, stream=None,
+                   plain: bool = False, check: bool = True) -> int:
+    """Decode with torch tensors as buffers (uint8 codes/out, int32 offsets)."""
+    fn = decode_plain if plain else decode
+    return fn(codec, d, codes.data_ptr(), codes.numel() * codes.element_size(), code_offsets.data_ptr(),
+              n_strings, out.data_ptr() if out.numel() else 0, out.numel() * out.element_size(),
+              out_offsets.data_ptr(), stream, check)
+
+
+def decoded_size_tensors(codec, d: Dict, codes, code_offsets, n_strings: int, stream=None) -> tuple[int, int]:
+    return decoded_size(codec, d, codes.data_ptr(), codes.numel() * codes.element_size(),
+                        code_offsets.data_ptr(), n_strings, stream)

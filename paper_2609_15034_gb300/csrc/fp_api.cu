@@ -1,0 +1,390 @@
+// Host side of the C ABI (include/fastpair.h): argument validation,
+// dictionary repacking and upload, per-stream workspaces, variant selection
+// and kernel launches.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fp_internal.h"
+
+namespace fp {
+namespace {
+
+thread_local std::string g_last_error;
+
+fp_status fail(fp_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+fp_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? FP_ERR_NOMEM : FP_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+bool valid_codec(int c) { return c == FP_ONPAIR16 || c == FP_ONPAIR12 || c == FP_FSST8; }
+
+// ---- per-stream workspace ----------------------------------------------------
+struct Workspace {
+    void* d_mem = nullptr;        // WsHeader + tile status words
+    size_t tiles_cap = 0;
+    uint64_t launches = 0;
+    uint32_t* d_plain = nullptr;  // scratch of the plain baseline
+    size_t plain_words = 0;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
+
+// Get (or grow) the workspace of (current device, stream).
+fp_status get_workspace(cudaStream_t stream, size_t tiles, size_t plain_words, Workspace** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace*& w = g_ws[{dev, stream}];
+    if (!w) w = new Workspace();
+    if (w->d_mem == nullptr || w->tiles_cap < tiles) {
+        size_t cap = w->tiles_cap ? w->tiles_cap : 1024;
+        while (cap < tiles) cap *= 2;
+        if (w->d_mem) {
+            e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(w->d_mem);
+            w->d_mem = nullptr;
+            w->tiles_cap = 0;
+        }
+        const size_t bytes = kWsHeaderBytes + cap * sizeof(unsigned long long);
+        e = cudaMalloc(&w->d_mem, bytes);
+        if (e != cudaSuccess) { w->d_mem = nullptr; return cuda_fail(e, "cudaMalloc(workspace)"); }
+        e = cudaMemset(w->d_mem, 0, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(workspace)");
+        unsigned one = 1;   // epoch 0 is reserved for "never written"
+        e = cudaMemcpy(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, epoch), &one, sizeof(one),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(epoch)");
+        w->tiles_cap = cap;
+        w->launches = 0;
+    }
+    if (plain_words && w->plain_words < plain_words) {
+        if (w->d_plain) {
+            e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(w->d_plain);
+            w->d_plain = nullptr;
+            w->plain_words = 0;
+        }
+        e = cudaMalloc(&w->d_plain, plain_words * sizeof(uint32_t));
+        if (e != cudaSuccess) { w->d_plain = nullptr; return cuda_fail(e, "cudaMalloc(plain scratch)"); }
+        w->plain_words = plain_words;
+    }
+    *out = w;
+    return FP_OK;
+}
+
+Workspace* find_workspace(cudaStream_t stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find({dev, stream});
+    return it == g_ws.end() ? nullptr : it->second;
+}
+
+// ---- variants and occupancy ----------------------------------------------------
+std::atomic<int> g_selected[4] = {{-1}, {-1}, {-1}, {-1}};
+
+int selected_variant(int codec) {
+    const int v = g_selected[codec].load();
+    return v >= 0 ? v : variant_default(codec);
+}
+
+struct DevInfo {
+    int sms = 0;
+    std::map<const void*, int> blocks_per_sm;
+};
+std::map<int, DevInfo> g_dev;
+
+fp_status grid_for(const Variant& var, int* grid_per_wave) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevInfo& di = g_dev[dev];
+    if (di.sms == 0) {
+        e = cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    auto it = di.blocks_per_sm.find(var.kernel);
+    if (it == di.blocks_per_sm.end()) {
+        e = cudaFuncSetAttribute(var.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)var.smem_bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, var.kernel, var.threads, var.smem_bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (nb < 1) return fail(FP_ERR_CUDA, "decode variant does not fit on an SM");
+        it = di.blocks_per_sm.emplace(var.kernel, nb).first;
+    }
+    *grid_per_wave = it->second * di.sms;
+    return FP_OK;
+}
+
+uint64_t max_slots_of(int codec, uint64_t codes_bytes) { return codes_bytes * 8 / code_bits(codec); }
+
+fp_status check_common(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                       const uint32_t* d_code_offsets, uint8_t* d_out_bytes, uint64_t out_capacity,
+                       uint32_t* d_out_offsets, bool need_out) {
+    if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
+    if (!dict) return fail(FP_ERR_ARG, "dict is NULL");
+    if (dict->codec != codec) return fail(FP_ERR_ARG, "dictionary codec %d != codec %d", dict->codec, (int)codec);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != dict->device)
+        return fail(FP_ERR_ARG, "dictionary lives on device %d, current device is %d", dict->device, dev);
+    if (!d_code_offsets) return fail(FP_ERR_ARG, "d_code_offsets is NULL");
+    if (reinterpret_cast<uintptr_t>(d_code_offsets) % 4) return fail(FP_ERR_ARG, "d_code_offsets not 4-byte aligned");
+    if (codes_bytes && !d_codes) return fail(FP_ERR_ARG, "d_codes is NULL");
+    if (reinterpret_cast<uintptr_t>(d_codes) % 16) return fail(FP_ERR_ARG, "d_codes not 16-byte aligned");
+    if (need_out) {
+        if (!d_out_offsets) return fail(FP_ERR_ARG, "d_out_offsets is NULL");
+        if (reinterpret_cast<uintptr_t>(d_out_offsets) % 4) return fail(FP_ERR_ARG, "d_out_offsets not 4-byte aligned");
+        if (out_capacity && !d_out_bytes) return fail(FP_ERR_ARG, "d_out_bytes is NULL");
+        if (reinterpret_cast<uintptr_t>(d_out_bytes) % 16) return fail(FP_ERR_ARG, "d_out_bytes not 16-byte aligned");
+    }
+    return FP_OK;
+}
+
+fp_status status_from_bits(uint32_t bits) {
+    if (bits & ERRB_TIMEOUT) return fail(FP_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (bits & ERRB_CORRUPT) return fail(FP_ERR_CORRUPT, "corrupt input (code >= n_entries, dangling escape or bad code_offsets)");
+    if (bits & ERRB_CAPACITY) return fail(FP_ERR_CAPACITY, "decoded size exceeds out_capacity");
+    if (bits & ERRB_OVERFLOW) return fail(FP_ERR_OVERFLOW, "decoded size exceeds 2^31-1");
+    return FP_OK;
+}
+
+// Read and clear the workspace status (stream already synchronised).
+fp_status take_status(Workspace* w, uint64_t* total) {
+    WsHeader h;
+    cudaError_t e = cudaMemcpy(&h, w->d_mem, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    if (h.status) {
+        e = cudaMemset(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, status), 0, sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+    }
+    if (total) *total = h.total;
+    return status_from_bits(h.status);
+}
+
+fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                     const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                     uint64_t out_capacity, uint32_t* d_out_offsets, cudaStream_t stream, bool size_only,
+                     Workspace** ws_out) {
+    const Variant* var = variant_get(codec, selected_variant(codec));
+    if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
+    const uint64_t max_slots = max_slots_of(codec, codes_bytes);
+    const uint64_t tile = (uint64_t)var->threads * var->slots_per_thread;
+    const uint64_t n_tiles = max_slots / tile + 2;
+    int per_wave = 0;
+    fp_status st = grid_for(*var, &per_wave);
+    if (st != FP_OK) return st;
+    Workspace* w = nullptr;
+    st = get_workspace(stream, n_tiles, 0, &w);
+    if (st != FP_OK) return st;
+    if ((++w->launches & ((1ull << 25) - 1)) == 0) {
+        // Tile status words carry a 26-bit launch tag; clear them well before it wraps.
+        cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(w->d_mem) + kWsHeaderBytes, 0,
+                                        w->tiles_cap * sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    DecodeParams p;
+    p.dict = dict->view();
+    p.codes = static_cast<const uint8_t*>(d_codes);
+    p.codes_bytes = codes_bytes;
+    p.max_slots = max_slots;
+    p.code_offsets = d_code_offsets;
+    p.n_strings = n_strings;
+    p.out = d_out_bytes;
+    p.capacity = size_only ? 0 : out_capacity;
+    p.out_offsets = d_out_offsets;
+    p.ws = static_cast<WsHeader*>(w->d_mem);
+    p.tile_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(w->d_mem) + kWsHeaderBytes);
+    p.size_only = size_only ? 1 : 0;
+    const uint64_t grid = n_tiles < (uint64_t)per_wave ? n_tiles : (uint64_t)per_wave;
+    cudaError_t e = launch_decode(codec, *var, p, (int)grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    if (ws_out) *ws_out = w;
+    return FP_OK;
+}
+
+}  // namespace
+}  // namespace fp
+
+using namespace fp;
+
+extern "C" {
+
+const char* fp_last_error(void) { return g_last_error.c_str(); }
+
+fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t* h_offsets,
+                         uint32_t n_entries, fp_stream_t stream_, fp_dict** out) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!out) return fail(FP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
+    if (!h_offsets || !h_bytes) return fail(FP_ERR_ARG, "h_bytes/h_offsets is NULL");
+    if (n_entries < 1 || n_entries > max_entries(codec))
+        return fail(FP_ERR_ARG, "n_entries %u out of range 1..%u", n_entries, max_entries(codec));
+    const uint32_t L = max_token(codec);
+    for (uint32_t i = 0; i < n_entries; ++i) {
+        if (h_offsets[i + 1] < h_offsets[i]) return fail(FP_ERR_ARG, "h_offsets decrease at %u", i);
+        const uint32_t len = h_offsets[i + 1] - h_offsets[i];
+        if (len < 1 || len > L) return fail(FP_ERR_ARG, "token %u has length %u (allowed 1..%u)", i, len, L);
+    }
+    const uint32_t n_tab = table_entries(codec), stride = table_stride(codec);
+    std::vector<uint8_t> table((size_t)n_tab * stride, 0), lens(n_tab, 0);
+    for (uint32_t i = 0; i < n_entries; ++i) {
+        const uint32_t a = h_offsets[i], len = h_offsets[i + 1] - a;
+        memcpy(&table[(size_t)i * stride], h_bytes + a, len);
+        lens[i] = (uint8_t)len;
+    }
+    const uint32_t base = h_offsets[0], nbytes = h_offsets[n_entries] - base;
+    std::vector<uint32_t> offs(n_entries + 1);
+    for (uint32_t i = 0; i <= n_entries; ++i) offs[i] = h_offsets[i] - base;
+
+    fp_dict* d = new fp_dict();
+    d->codec = codec;
+    d->n_entries = n_entries;
+    d->table_bytes = table.size();
+    cudaError_t e = cudaGetDevice(&d->device);
+    if (e == cudaSuccess) e = cudaMalloc(&d->d_table, table.size());
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->d_lens), lens.size());
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->d_bytes), nbytes ? nbytes : 1);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->d_offsets), offs.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d->d_table, table.data(), table.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d->d_lens, lens.data(), lens.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && nbytes)
+        e = cudaMemcpyAsync(d->d_bytes, h_bytes + base, nbytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d->d_offsets, offs.data(), offs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        fp_dict_free(d);
+        return cuda_fail(e, "dictionary upload");
+    }
+    *out = d;
+    return FP_OK;
+}
+
+fp_status fp_dict_free(fp_dict* d) {
+    if (!d) return FP_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(d->device);
+    cudaDeviceSynchronize();
+    cudaFree(d->d_table);
+    cudaFree(d->d_lens);
+    cudaFree(d->d_bytes);
+    cudaFree(d->d_offsets);
+    cudaSetDevice(prev);
+    delete d;
+    return FP_OK;
+}
+
+fp_status fp_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                    const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                    uint64_t out_capacity, uint32_t* d_out_offsets, fp_stream_t stream) {
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, d_out_bytes, out_capacity,
+                                d_out_offsets, true);
+    if (st != FP_OK) return st;
+    return run_decode(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_out_bytes, out_capacity,
+                      d_out_offsets, reinterpret_cast<cudaStream_t>(stream), false, nullptr);
+}
+
+fp_status fp_decoded_size(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                          const uint32_t* d_code_offsets, uint32_t n_strings, fp_stream_t stream_,
+                          uint64_t* h_total) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!h_total) return fail(FP_ERR_ARG, "h_total is NULL");
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, nullptr, 0, nullptr, false);
+    if (st != FP_OK) return st;
+    Workspace* w = nullptr;
+    st = run_decode(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, nullptr, 0, nullptr, stream,
+                    true, &w);
+    if (st != FP_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return take_status(w, h_total);
+}
+
+fp_status fp_decode_plain(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                          const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                          uint64_t out_capacity, uint32_t* d_out_offsets, fp_stream_t stream_) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, d_out_bytes, out_capacity,
+                                d_out_offsets, true);
+    if (st != FP_OK) return st;
+    Workspace* w = nullptr;
+    const size_t words = plain_scratch_words(n_strings);
+    st = get_workspace(stream, 1, words, &w);
+    if (st != FP_OK) return st;
+    DecodeParams p;
+    memset(&p, 0, sizeof(p));
+    p.dict = dict->view();
+    p.codes = static_cast<const uint8_t*>(d_codes);
+    p.codes_bytes = codes_bytes;
+    p.max_slots = max_slots_of(codec, codes_bytes);
+    p.code_offsets = d_code_offsets;
+    p.n_strings = n_strings;
+    p.out = d_out_bytes;
+    p.capacity = out_capacity;
+    p.out_offsets = d_out_offsets;
+    p.ws = static_cast<WsHeader*>(w->d_mem);
+    p.size_only = 0;
+    cudaError_t e = launch_plain(codec, p, w->d_plain, w->plain_words, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "plain decode launch");
+    return FP_OK;
+}
+
+fp_status fp_sync_status(fp_stream_t stream_) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    Workspace* w = find_workspace(stream);
+    if (!w || !w->d_mem) return FP_OK;
+    return take_status(w, nullptr);
+}
+
+int fp_variant_count(fp_codec codec) { return valid_codec(codec) ? variant_count(codec) : 0; }
+
+fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* slots_per_thread,
+                          uint32_t* dict_in_smem) {
+    if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
+    const Variant* var = variant_get(codec, v);
+    if (!var) return fail(FP_ERR_ARG, "variant %d out of range", v);
+    if (threads) *threads = (uint32_t)var->threads;
+    if (slots_per_thread) *slots_per_thread = (uint32_t)var->slots_per_thread;
+    if (dict_in_smem) *dict_in_smem = (uint32_t)var->dict_smem;
+    return FP_OK;
+}
+
+fp_status fp_variant_select(fp_codec codec, int v) {
+    if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
+    if (v != -1 && !variant_get(codec, v)) return fail(FP_ERR_ARG, "variant %d out of range", v);
+    g_selected[codec].store(v);
+    return FP_OK;
+}
+
+int fp_variant_selected(fp_codec codec) { return valid_codec(codec) ? selected_variant(codec) : -1; }
+
+}  // extern "C"
