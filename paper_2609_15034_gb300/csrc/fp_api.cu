@@ -67,7 +67,7 @@ fp_status get_workspace(cudaStream_t stream, size_t tiles, size_t plain_words, W
             w->d_mem = nullptr;
             w->tiles_cap = 0;
         }
-        const size_t bytes = kWsHeaderBytes + cap * sizeof(unsigned long long);
+        const size_t bytes = kWsHeaderBytes + cap * sizeof(unsigned long long) + (cap + 1) * sizeof(uint32_t);
         e = cudaMalloc(&w->d_mem, bytes);
         if (e != cudaSuccess) { w->d_mem = nullptr; return cuda_fail(e, "cudaMalloc(workspace)"); }
         e = cudaMemset(w->d_mem, 0, bytes);
@@ -192,8 +192,9 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
                      Workspace** ws_out) {
     const Variant* var = variant_get(codec, selected_variant(codec));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
+    if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
     const uint64_t max_slots = max_slots_of(codec, codes_bytes);
-    const uint64_t tile = (uint64_t)var->threads * var->slots_per_thread;
+    const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
     int per_wave = 0;
     fp_status st = grid_for(*var, &per_wave);
@@ -221,7 +222,9 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
     p.tile_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(w->d_mem) + kWsHeaderBytes);
     p.size_only = size_only ? 1 : 0;
     const uint64_t grid = n_tiles < (uint64_t)per_wave ? n_tiles : (uint64_t)per_wave;
-    cudaError_t e = launch_decode(codec, *var, p, (int)grid, stream);
+    uint32_t* first = reinterpret_cast<uint32_t*>(static_cast<char*>(w->d_mem) + kWsHeaderBytes +
+                                                  w->tiles_cap * sizeof(unsigned long long));
+    cudaError_t e = launch_decode(codec, *var, p, first, (int)grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     if (ws_out) *ws_out = w;
     return FP_OK;

@@ -14,14 +14,15 @@ constexpr uint32_t ERRB_CAPACITY = 2u;
 constexpr uint32_t ERRB_OVERFLOW = 4u;
 constexpr uint32_t ERRB_TIMEOUT = 8u;
 
-// Device workspace header (one per stream).  The tile status words of the
-// single-pass prefix scan follow it at `kWsHeaderBytes`.
+// Device workspace header (one per stream).  It is followed by the tile
+// status words of the single-pass prefix scan (one u64 per tile, at
+// `kWsHeaderBytes`) and by the tile -> first string index (tiles + 1 u32).
 struct WsHeader {
     unsigned int tile_counter;   // next tile ticket
     unsigned int exit_counter;   // blocks that have finished
     unsigned int epoch;          // launch generation tag of tile status words
     unsigned int status;         // sticky ERRB_* bits
-    unsigned long long covered;  // string boundaries written this launch
+    unsigned long long reserved;
     unsigned long long total;    // decoded size of the last launch
     unsigned int abort;          // set when a bounded wait gave up
     unsigned int pad[23];
@@ -71,7 +72,8 @@ const Variant* variant_get(int codec, int v);
 int variant_default(int codec);
 
 // Launch helpers (fp_decode.cu, fp_plain.cu).
-cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p, int grid,
+uint64_t variant_tile(const Variant& v);   // code slots per tile
+cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p, uint32_t* first, int grid,
                           cudaStream_t stream);
 cudaError_t launch_plain(int codec, const DecodeParams& p, uint32_t* d_scratch, size_t scratch_words,
                          cudaStream_t stream);
