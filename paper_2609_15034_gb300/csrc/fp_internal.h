@@ -64,6 +64,7 @@ struct Variant {
     int dict_smem;
     size_t smem_bytes;
     const void* kernel;   // __global__ function
+    int work_threads;     // threads that assemble output (slots per tile = work_threads * slots_per_thread)
 };
 
 // Variant tables (fp_decode.cu).
