@@ -174,6 +174,40 @@ fp_status fp_sync_status(fp_stream_t stream);
 const char* fp_last_error(void);
 
 /*
+ * fp_decode_noalloc -- fp_decode for callers that cannot allocate.
+ *
+ * This entry point has no counterpart in the paper.  It exists for callers
+ * that cannot call cudaMalloc -- an allocator hook, or an engine that owns
+ * every byte of device memory and forbids allocations behind its back --
+ * since fp_decode allocates its per-stream workspace on first use.  Its
+ * scratch is a
+ * fixed 1 MiB array compiled into the library; every GPU that loads the
+ * library keeps that array until the process exits.  The call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Arguments, layout and result are those of fp_decode, plus:
+ *   d_status   device, one uint32 written (stream-ordered) with the call's
+ *              data-error bits: 0 = OK; 1 = corrupt input, 2 = decoded size
+ *              above out_capacity, 4 = above 2^31-1, 8 = a bounded device
+ *              wait gave up.  fp_sync_status does not report these calls.
+ *
+ * Limits and sharing:
+ *   - the code buffer may span at most the tiles the scratch holds
+ *     (87,370 tiles minus 2: about 357M slots with the default tile of 4,096
+ *     slots); larger inputs return FP_ERR_ARG with the limit in
+ *     fp_last_error() -- use fp_decode for them.
+ *   - the first call on a device looks up and clears the array
+ *     (synchronously); make that first call before any stream capture.
+ *   - every call, on any stream, shares the one array per device: calls
+ *     that overlap on the GPU race and corrupt each other's results.
+ *     Serialise them (one stream, or events).
+ */
+fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                            const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                            uint64_t out_capacity, uint32_t* d_out_offsets, uint32_t* d_status,
+                            fp_stream_t stream);
+
+/*
  * Decode variants (tile shapes).  A variant fixes the threads per block, the
  * code slots each thread decodes and where the dictionary is read from
  * (shared memory staged once per block, or the L1/L2 cache path).

@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
             L.fp_decode.argtypes = [I, P, P, U64, P, U32, P, U64, P, P]
             L.fp_decode_plain.argtypes = [I, P, P, U64, P, U32, P, U64, P, P]
             L.fp_decoded_size.argtypes = [I, P, P, U64, P, U32, P, ctypes.POINTER(U64)]
+            L.fp_decode_noalloc.argtypes = [I, P, P, U64, P, U32, P, U64, P, P, P]
             L.fp_sync_status.argtypes = [P]
             L.fp_last_error.restype = ctypes.c_char_p
             L.fp_variant_count.argtypes = [I]
@@ -64,6 +65,7 @@ def lib() -> ctypes.CDLL:
             L.fp_variant_select.argtypes = [I, I]
             L.fp_variant_selected.argtypes = [I]
             for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
+                         "fp_decode_noalloc",
                          "fp_sync_status", "fp_variant_info", "fp_variant_select"):
                 getattr(L, name).restype = I
             _lib = L
@@ -137,6 +139,16 @@ def decode_plain(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_
     st = lib().fp_decode_plain(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr,
                                capacity, out_offsets_ptr, _stream(stream))
     return _check(st, "fp_decode_plain") if check else st
+
+
+def decode_noalloc(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                   out_ptr: int, capacity: int, out_offsets_ptr: int, status_ptr: int, stream=None,
+                   check: bool = True) -> int:
+    """fp_decode_noalloc: decode with the library's fixed scratch (no device
+    allocation); the call's data-error bits land in the uint32 at status_ptr."""
+    st = lib().fp_decode_noalloc(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr,
+                                 capacity, out_offsets_ptr, status_ptr, _stream(stream))
+    return _check(st, "fp_decode_noalloc") if check else st
 
 
 def decoded_size(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,

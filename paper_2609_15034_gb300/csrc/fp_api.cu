@@ -391,3 +391,114 @@ fp_status fp_variant_select(fp_codec codec, int v) {
 int fp_variant_selected(fp_codec codec) { return valid_codec(codec) ? selected_variant(codec) : -1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Decoding without allocation.
+//
+// Some callers cannot call cudaMalloc at all: an allocator hook, or an
+// embedding engine that owns all device memory and forbids other
+// allocations.  fp_decode_noalloc serves them: its
+// scratch (the workspace header, one status word per tile and the tile ->
+// first string index) lives in the fixed array below, which every GPU that
+// loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 1u << 20;   // 1 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+    bool ready = false;
+    void* ptr = nullptr;        // device address of g_noalloc_scratch on this device
+    uint64_t launches = 0;
+};
+std::mutex g_noalloc_mu;
+std::map<int, NoAllocDevice> g_noalloc;
+
+// Once per device, with that device current: look up the array's device
+// address (in host code its name only stands for it) and initialise it.
+fp_status noalloc_setup(NoAllocDevice** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        e = cudaMemset(ptr, 0, kNoAllocScratchBytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(scratch)");
+        const unsigned one = 1;   // launch tag 0 means "never written"
+        e = cudaMemcpy(static_cast<char*>(ptr) + offsetof(WsHeader, epoch), &one, sizeof(one),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(scratch epoch)");
+        d.ptr = ptr;
+        d.ready = true;
+    }
+    *out = &d;
+    return FP_OK;
+}
+
+}  // namespace
+
+extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, const void* d_codes,
+                                       uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                                       uint8_t* d_out_bytes, uint64_t out_capacity, uint32_t* d_out_offsets,
+                                       uint32_t* d_status, fp_stream_t stream_) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, d_out_bytes, out_capacity,
+                                d_out_offsets, true);
+    if (st != FP_OK) return st;
+    if (!d_status || reinterpret_cast<uintptr_t>(d_status) % 4) return fail(FP_ERR_ARG, "d_status must be a 4-byte aligned device pointer");
+    if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
+    const Variant* var = variant_get(codec, selected_variant(codec));
+    if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
+    const uint64_t max_slots = max_slots_of(codec, codes_bytes);
+    const uint64_t tile = variant_tile(*var);
+    const uint64_t n_tiles = max_slots / tile + 2;
+    const uint64_t cap = (kNoAllocScratchBytes - kWsHeaderBytes - sizeof(uint32_t)) /
+                         (sizeof(unsigned long long) + sizeof(uint32_t));
+    if (n_tiles > cap)
+        return fail(FP_ERR_ARG,
+                    "fp_decode_noalloc: the code buffer spans up to %llu tiles of %llu slots; the fixed scratch holds "
+                    "%llu tiles (%llu slots); use fp_decode",
+                    (unsigned long long)n_tiles, (unsigned long long)tile, (unsigned long long)cap,
+                    (unsigned long long)((cap - 2) * tile));
+    int per_wave = 0;
+    st = grid_for(*var, &per_wave);
+    if (st != FP_OK) return st;
+    NoAllocDevice* nd = nullptr;
+    st = noalloc_setup(&nd);
+    if (st != FP_OK) return st;
+    char* base = static_cast<char*>(nd->ptr);
+    cudaError_t e;
+    if ((++nd->launches & ((1ull << 25) - 1)) == 0) {
+        // tile status words carry a 26-bit launch tag; clear them well before it wraps
+        e = cudaMemsetAsync(base + kWsHeaderBytes, 0, cap * sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
+    }
+    DecodeParams p;
+    p.dict = dict->view();
+    p.codes = static_cast<const uint8_t*>(d_codes);
+    p.codes_bytes = codes_bytes;
+    p.max_slots = max_slots;
+    p.code_offsets = d_code_offsets;
+    p.n_strings = n_strings;
+    p.out = d_out_bytes;
+    p.capacity = out_capacity;
+    p.out_offsets = d_out_offsets;
+    p.ws = reinterpret_cast<WsHeader*>(base);
+    p.tile_status = reinterpret_cast<unsigned long long*>(base + kWsHeaderBytes);
+    p.size_only = 0;
+    uint32_t* first = reinterpret_cast<uint32_t*>(base + kWsHeaderBytes + cap * sizeof(unsigned long long));
+    const uint64_t grid = n_tiles < (uint64_t)per_wave ? n_tiles : (uint64_t)per_wave;
+    e = launch_decode(codec, *var, p, first, (int)grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    // hand the call's data-error bits to the caller and clear them for the next call
+    e = cudaMemcpyAsync(d_status, base + offsetof(WsHeader, status), sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                        stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + offsetof(WsHeader, status), 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    return FP_OK;
+}
