@@ -350,7 +350,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": load_traffic(args.workload), "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": round(avg_launch_s * 1e3, 4)},
         "clocks": clocks,
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,   # per step: the index pass and the decode kernel
     }
     line.update(extra)
     if "e2e" not in line:
