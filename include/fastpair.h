@@ -208,6 +208,97 @@ fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, const void* d_c
                             fp_stream_t stream);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Batched decode (no counterpart API in the paper, which decodes one column
+ * per launch): many chunks -- each a column as fp_decode takes it, with its
+ * own codec and dictionary -- decoded by one persistent kernel launch that
+ * takes (chunk, tile) work items from device-side queues, replayed from a
+ * CUDA graph.  Each chunk's result is exactly fp_decode's.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct fp_chunk {
+    fp_codec codec;
+    const fp_dict* dict;
+    const void* d_codes;              /* as fp_decode (16-byte aligned)            */
+    uint64_t codes_bytes;
+    const uint32_t* d_code_offsets;   /* n_strings + 1 slot indices                */
+    uint32_t n_strings;
+    uint8_t* d_out_bytes;             /* 16-byte aligned                           */
+    uint64_t out_capacity;
+    uint32_t* d_out_offsets;          /* n_strings + 1                             */
+} fp_chunk;
+
+typedef struct fp_plan fp_plan;   /* opaque, library-owned */
+
+/*
+ * fp_plan_create -- validate the chunks, pick a tile configuration and
+ * capture the batch into a CUDA graph.  Synchronous.
+ *
+ *   chunks           host array of n_chunks descriptors (copied; the device
+ *                    buffers they name must stay valid while the plan is used,
+ *                    and the dictionaries must outlive the plan).
+ *   n_chunks         >= 1.
+ *   tune_cache_path  NULL, or a text file: if it holds a configuration for
+ *                    this plan's signature (SM count and the multiset of
+ *                    (codec, half-octave of code slots)), it is used;
+ *                    otherwise every configuration is timed on the plan's
+ *                    own chunks and the fastest is appended to the file.
+ *                    Tuning runs decode the chunks, writing their outputs.
+ *   stream           stream of the tuning runs.
+ *
+ * The chunks' code buffers are tiled whole, so pass code buffers that start
+ * close to each chunk's first slot.  Errors: FP_ERR_ARG (a chunk fails the
+ * checks of fp_decode, n_chunks == 0), FP_ERR_NOMEM, FP_ERR_CUDA.
+ */
+fp_status fp_plan_create(const fp_chunk* chunks, uint32_t n_chunks, const char* tune_cache_path,
+                         fp_stream_t stream, fp_plan** out);
+
+/* fp_plan_create with configuration `config` (0 .. fp_batch_config_count()-1), no tuning. */
+fp_status fp_plan_create_config(const fp_chunk* chunks, uint32_t n_chunks, int config, fp_stream_t stream,
+                                fp_plan** out);
+
+/*
+ * fp_decode_batch -- decode every chunk of the plan (one graph launch on
+ * `stream`).  Asynchronous.  Launches of one plan must not overlap (they
+ * share its device state); use one stream or events.  Data errors are
+ * recorded per chunk; read them with fp_plan_sync_status.
+ */
+fp_status fp_decode_batch(fp_plan* plan, fp_stream_t stream);
+
+/*
+ * fp_plan_sync_status -- synchronise `stream`, then read and clear the
+ * plan's per-chunk data status.  h_chunk_status (optional, n_chunks
+ * entries) receives each chunk's fp_status; h_chunk_total (optional)
+ * each chunk's decoded size from its last decode.  Returns the most severe
+ * status over all chunks (priority as fp_sync_status).
+ */
+fp_status fp_plan_sync_status(fp_plan* plan, fp_stream_t stream, uint32_t* h_chunk_status,
+                              uint64_t* h_chunk_total);
+
+typedef struct fp_plan_info_t {
+    uint32_t config;               /* chosen configuration                      */
+    uint32_t n_configs;            /* configurations compiled in                */
+    uint32_t slots_per_thread[3];  /* OnPair-16, OnPair-12, FSST-8              */
+    uint32_t threads;              /* threads per block                         */
+    uint32_t grid;                 /* blocks of the persistent launch           */
+    uint32_t index_blocks;         /* blocks of the index pass                  */
+    uint32_t from_cache;           /* 1 if the configuration came from the file */
+    uint32_t reserved;
+    uint64_t total_tiles;
+    uint64_t layout_bytes;         /* device bytes of the plan's tables         */
+    float tune_ms[8];              /* tuning time per configuration, -1 = untimed */
+} fp_plan_info_t;
+
+fp_status fp_plan_info(const fp_plan* plan, fp_plan_info_t* info);
+
+/* Release a plan (synchronises the device first).  NULL is a no-op. */
+fp_status fp_plan_destroy(fp_plan* plan);
+
+/* Batch configurations: slots per thread per codec and blocks per SM. */
+int fp_batch_config_count(void);
+fp_status fp_batch_config_info(int config, uint32_t* slots_per_thread3, uint32_t* blocks_per_sm);
+
+/*
  * Decode variants (tile shapes).  A variant fixes the threads per block, the
  * code slots each thread decodes and where the dictionary is read from
  * (shared memory staged once per block, or the L1/L2 cache path).

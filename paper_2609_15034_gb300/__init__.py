@@ -64,9 +64,18 @@ def lib() -> ctypes.CDLL:
             L.fp_variant_info.argtypes = [I, I, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32)]
             L.fp_variant_select.argtypes = [I, I]
             L.fp_variant_selected.argtypes = [I]
+            L.fp_plan_create.argtypes = [ctypes.POINTER(Chunk), U32, ctypes.c_char_p, P, ctypes.POINTER(P)]
+            L.fp_plan_create_config.argtypes = [ctypes.POINTER(Chunk), U32, I, P, ctypes.POINTER(P)]
+            L.fp_decode_batch.argtypes = [P, P]
+            L.fp_plan_sync_status.argtypes = [P, P, P, P]
+            L.fp_plan_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+            L.fp_plan_destroy.argtypes = [P]
+            L.fp_batch_config_info.argtypes = [I, P, ctypes.POINTER(U32)]
             for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
                          "fp_decode_noalloc",
-                         "fp_sync_status", "fp_variant_info", "fp_variant_select"):
+                         "fp_sync_status", "fp_variant_info", "fp_variant_select",
+                         "fp_plan_create", "fp_plan_create_config", "fp_decode_batch", "fp_plan_sync_status",
+                         "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib
@@ -88,6 +97,23 @@ def _stream(s) -> ctypes.c_void_p:
     if hasattr(s, "cuda_stream"):
         s = s.cuda_stream
     return ctypes.c_void_p(int(s))
+
+
+class Chunk(ctypes.Structure):
+    """fp_chunk: one column of a batch (device addresses as integers)."""
+    _fields_ = [("codec", ctypes.c_int), ("dict", ctypes.c_void_p), ("d_codes", ctypes.c_void_p),
+                ("codes_bytes", ctypes.c_uint64), ("d_code_offsets", ctypes.c_void_p),
+                ("n_strings", ctypes.c_uint32), ("d_out_bytes", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_uint64), ("d_out_offsets", ctypes.c_void_p)]
+
+
+class PlanInfo(ctypes.Structure):
+    """fp_plan_info_t."""
+    _fields_ = [("config", ctypes.c_uint32), ("n_configs", ctypes.c_uint32),
+                ("slots_per_thread", ctypes.c_uint32 * 3), ("threads", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("index_blocks", ctypes.c_uint32), ("from_cache", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("total_tiles", ctypes.c_uint64), ("layout_bytes", ctypes.c_uint64),
+                ("tune_ms", ctypes.c_float * 8)]
 
 
 class Dict:
@@ -196,3 +222,86 @@ def decode_tensors(codec, d: Dict, codes, code_offsets, n_strings: int, out, out
 def decoded_size_tensors(codec, d: Dict, codes, code_offsets, n_strings: int, stream=None) -> tuple[int, int]:
     return decoded_size(codec, d, codes.data_ptr(), codes.numel() * codes.element_size(),
                         code_offsets.data_ptr(), n_strings, stream)
+
+
+# ---- batched decode (fp_plan_*) ----------------------------------------------
+
+def chunk(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+          out_ptr: int, capacity: int, out_offsets_ptr: int) -> Chunk:
+    return Chunk(codec, d.handle.value, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr or None,
+                 capacity, out_offsets_ptr)
+
+
+def chunk_tensors(codec, d: Dict, codes, code_offsets, n_strings: int, out, out_offsets) -> Chunk:
+    """fp_chunk from torch tensors (uint8 codes/out, int32 offsets)."""
+    return chunk(codec, d, codes.data_ptr(), codes.numel() * codes.element_size(), code_offsets.data_ptr(),
+                 n_strings, out.data_ptr() if out.numel() else 0, out.numel() * out.element_size(),
+                 out_offsets.data_ptr())
+
+
+class Plan:
+    """fp_plan: a batch of chunks decoded by one graph launch.
+
+    ``config=None`` tunes (optionally remembering the choice in
+    ``tune_cache``); an integer fixes the configuration."""
+
+    def __init__(self, chunks, tune_cache: str | None = None, config: int | None = None, stream=None):
+        arr = (Chunk * len(chunks))(*chunks)
+        self._keep = (arr, list(chunks))
+        self.n_chunks = len(chunks)
+        h = ctypes.c_void_p()
+        if config is None:
+            path = tune_cache.encode() if tune_cache else None
+            _check(lib().fp_plan_create(arr, len(chunks), path, _stream(stream), ctypes.byref(h)), "fp_plan_create")
+        else:
+            _check(lib().fp_plan_create_config(arr, len(chunks), int(config), _stream(stream), ctypes.byref(h)),
+                   "fp_plan_create_config")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise ValueError("plan was destroyed")
+        return self._h
+
+    def decode(self, stream=None, check: bool = True) -> int:
+        st = lib().fp_decode_batch(self.handle, _stream(stream))
+        return _check(st, "fp_decode_batch") if check else st
+
+    def sync_status(self, stream=None):
+        """Returns (status, per-chunk status array, per-chunk decoded sizes)."""
+        sts = np.zeros(self.n_chunks, np.uint32)
+        tot = np.zeros(self.n_chunks, np.uint64)
+        st = lib().fp_plan_sync_status(self.handle, _stream(stream), sts.ctypes.data, tot.ctypes.data)
+        return st, sts, tot
+
+    def info(self) -> dict:
+        pi = PlanInfo()
+        _check(lib().fp_plan_info(self.handle, ctypes.byref(pi)), "fp_plan_info")
+        return {"config": pi.config, "n_configs": pi.n_configs, "slots_per_thread": list(pi.slots_per_thread),
+                "threads": pi.threads, "grid": pi.grid, "index_blocks": pi.index_blocks,
+                "from_cache": bool(pi.from_cache), "total_tiles": pi.total_tiles, "layout_bytes": pi.layout_bytes,
+                "tune_ms": [round(float(x), 4) for x in list(pi.tune_ms)[:pi.n_configs]]}
+
+    def destroy(self):
+        if self._h is not None and _lib is not None:
+            _lib.fp_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def batch_config_count() -> int:
+    return lib().fp_batch_config_count()
+
+
+def batch_config_info(config: int) -> dict:
+    k = (ctypes.c_uint32 * 3)()
+    b = ctypes.c_uint32()
+    _check(lib().fp_batch_config_info(config, ctypes.cast(k, ctypes.c_void_p), ctypes.byref(b)),
+           "fp_batch_config_info")
+    return {"slots_per_thread": list(k), "blocks_per_sm": b.value}

@@ -16,9 +16,10 @@
 #include "fp_internal.h"
 
 namespace fp {
-namespace {
 
+namespace {
 thread_local std::string g_last_error;
+}  // namespace
 
 fp_status fail(fp_status st, const char* fmt, ...) {
     char buf[512];
@@ -36,6 +37,8 @@ fp_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool valid_codec(int c) { return c == FP_ONPAIR16 || c == FP_ONPAIR12 || c == FP_FSST8; }
+
+namespace {
 
 // ---- per-stream workspace ----------------------------------------------------
 struct Workspace {
@@ -141,6 +144,8 @@ fp_status grid_for(const Variant& var, int* grid_per_wave) {
     return FP_OK;
 }
 
+}  // namespace
+
 uint64_t max_slots_of(int codec, uint64_t codes_bytes) { return codes_bytes * 8 / code_bits(codec); }
 
 fp_status check_common(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
@@ -172,6 +177,16 @@ fp_status status_from_bits(uint32_t bits) {
     if (bits & ERRB_OVERFLOW) return fail(FP_ERR_OVERFLOW, "decoded size exceeds 2^31-1");
     return FP_OK;
 }
+
+fp_status status_code(uint32_t bits) {
+    if (bits & ERRB_TIMEOUT) return FP_ERR_TIMEOUT;
+    if (bits & ERRB_CORRUPT) return FP_ERR_CORRUPT;
+    if (bits & ERRB_CAPACITY) return FP_ERR_CAPACITY;
+    if (bits & ERRB_OVERFLOW) return FP_ERR_OVERFLOW;
+    return FP_OK;
+}
+
+namespace {
 
 // Read and clear the workspace status (stream already synchronised).
 fp_status take_status(Workspace* w, uint64_t* total) {

@@ -6,6 +6,8 @@
 
 #include "fastpair.h"
 
+struct fp_dict;
+
 namespace fp {
 
 // Sticky data-error bits in the per-stream status word.
@@ -25,7 +27,8 @@ struct WsHeader {
     unsigned long long reserved;
     unsigned long long total;    // decoded size of the last launch
     unsigned int abort;          // set when a bounded wait gave up
-    unsigned int pad[23];
+    unsigned int queue_counter[3];   // batched decode: next tile ticket of each codec queue
+    unsigned int pad[20];
 };
 constexpr size_t kWsHeaderBytes = 128;
 static_assert(sizeof(WsHeader) == kWsHeaderBytes, "workspace header size");
@@ -52,9 +55,46 @@ struct DecodeParams {
     uint8_t* out;
     uint64_t capacity;
     uint32_t* out_offsets;
-    WsHeader* ws;
-    unsigned long long* tile_status;
+    WsHeader* ws;                     // launch-wide counters, launch tag, abort flag
+    unsigned long long* tile_status;  // look-back words of this column's tiles (tile 0 first)
     int size_only;
+    unsigned int* err_word;           // where this column's data-error bits go
+    unsigned long long* total_out;    // where this column's decoded size goes
+    const uint32_t* first;            // tile -> first string boundary it owns (index pass)
+};
+
+// Tiles of a column: a tile is `tile` consecutive code slots, tile u covers
+// slots [(first_tile + u) * tile, ...); the column's slots are [c_begin, c_end).
+struct Extent {
+    unsigned long long c_begin, c_end, first_tile, n_tiles;
+    unsigned int bad;   // code_offsets[0] / [n] inconsistent with the code buffer
+    unsigned int pad;
+};
+
+// Batched decode: one record per chunk, copied into a decode block's shared
+// memory for every tile it takes.  The host fills `p` and `x.first_tile` /
+// `x.n_tiles` (the chunk's code buffer is tiled whole); the index pass fills
+// x.c_begin, x.c_end and x.bad.
+struct alignas(16) SlotSrc {
+    DecodeParams p;
+    Extent x;
+    uint32_t tile_base;   // queue ticket of the chunk's first tile
+    uint32_t chunk;       // index of the chunk in the plan
+};
+static_assert(sizeof(SlotSrc) % 16 == 0, "chunk records are copied in 16-byte pieces");
+
+// One codec's work queue: tickets 0..n_tiles-1 over its chunks' tiles.
+struct BatchQueue {
+    const SlotSrc* src;          // chunk records of this codec
+    const uint32_t* tile_chunk;  // ticket -> index into src
+    uint32_t n_tiles;
+    uint32_t n_chunks;
+};
+
+struct BatchParams {
+    WsHeader* ws;
+    BatchQueue q[3];      // OnPair-16, OnPair-12, FSST-8
+    uint32_t split[2];    // blocks [0, split[0]) start on queue 0, [split[0], split[1]) on 1, the rest on 2
 };
 
 // A compiled tile shape.
@@ -79,6 +119,17 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p, 
 cudaError_t launch_plain(int codec, const DecodeParams& p, uint32_t* d_scratch, size_t scratch_words,
                          cudaStream_t stream);
 size_t plain_scratch_words(uint32_t n_strings);
+
+// Host helpers (fp_api.cu).
+fp_status fail(fp_status st, const char* fmt, ...);          // sets fp_last_error()
+fp_status cuda_fail(cudaError_t e, const char* what);
+bool valid_codec(int c);
+uint64_t max_slots_of(int codec, uint64_t codes_bytes);
+fp_status check_common(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                       const uint32_t* d_code_offsets, uint8_t* d_out_bytes, uint64_t out_capacity,
+                       uint32_t* d_out_offsets, bool need_out);
+fp_status status_from_bits(uint32_t bits);                    // with an fp_last_error() text
+fp_status status_code(uint32_t bits);                         // without
 
 inline uint32_t code_bits(int codec) {
     return codec == FP_ONPAIR16 ? 16u : codec == FP_ONPAIR12 ? 12u : codec == FP_FSST8 ? 8u : 0u;
