@@ -34,7 +34,17 @@ WORKLOADS = {
     "onpair16_100k": (synth.ONPAIR16, 100_000,
                       "OnPair-16, 65,536-entry dictionary, 100k strings of 1-40 codes, Zipf(1.1)"),
 }
+# batched workloads: name -> (chunks, smallest and largest decoded chunk size, description)
+BATCH_WORKLOADS = {
+    "batched_4096": (4096, 4 << 10, 64 << 20,
+                     "4,096 chunks, OnPair-16/OnPair-12/FSST-8 2:1:1, one dictionary each, decoded sizes "
+                     "log-uniform 4 KB-64 MB, one persistent launch (CUDA graph)"),
+    "batched_4096_16mb": (4096, 4 << 10, 16 << 20,
+                          "4,096 chunks, OnPair-16/OnPair-12/FSST-8 2:1:1, one dictionary each, decoded sizes "
+                          "log-uniform 4 KB-16 MB, one persistent launch (CUDA graph)"),
+}
 METRIC = "decoded GB/s (single-column decode, inputs resident in HBM)"
+BATCH_METRIC = "decoded GB/s (batched decode of many chunks, inputs resident in HBM)"
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -360,12 +370,324 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Batched decode
+# ---------------------------------------------------------------------------
+
+POOL_STRINGS = {synth.ONPAIR16: 1_000_000, synth.ONPAIR12: 1_000_000, synth.FSST8: 2_000_000}
+
+
+class BatchInputs:
+    """Host side of a batch: per-codec pools of code streams and, per chunk,
+    its codec, its own dictionary and a window of its codec's pool."""
+
+    def __init__(self, n_chunks: int, lo: int, hi: int, seed: int = 0):
+        rng = synth.rng_for(4, seed, 0)
+        self.codecs = synth.codec_mix(rng, n_chunks)
+        targets = synth.log_uniform_sizes(rng, n_chunks, lo, hi)
+        self.pools = {c: synth.column(c, 1000 + seed, POOL_STRINGS[c]) for c in (synth.ONPAIR16, synth.ONPAIR12,
+                                                                                 synth.FSST8)}
+        per_string = {}
+        for c, pool in self.pools.items():
+            lens = pool.dictionary.token_lengths()
+            if c == synth.FSST8:
+                dec = int(np.where(pool.slot_is_literal, 1, np.where(pool.slot_codes == 255, 0,
+                                   lens[np.minimum(pool.slot_codes, lens.size - 1)])).sum())
+            else:
+                dec = int(lens[pool.slot_codes].sum())
+            per_string[c] = dec / pool.n_strings
+        bases = [synth.onpair12_dictionary(s) for s in range(8)]
+        self.chunks = []
+        for i in range(n_chunks):
+            c = int(self.codecs[i])
+            pool = self.pools[c]
+            n = int(max(1, min(pool.n_strings, round(targets[i] / per_string[c]))))
+            start = int(rng.integers(0, pool.n_strings - n + 1))
+            b0, b1, co = synth.pool_window(pool, start, n)
+            d = synth.chunk_dictionary(c, 10_000 + i, bases)
+            self.chunks.append((c, d, b0, b1, co))
+
+    def host_column(self, i):
+        c, d, b0, b1, co = self.chunks[i]
+        return synth.Column(c, d, self.pools[c].stream[b0:b1], co, (b1 - b0) * 8 // synth.CODE_BITS[c])
+
+
+def _align(x: int, a: int = 256) -> int:
+    return (x + a - 1) // a * a
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+    import paper_2609_15034_gb300 as fp
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    n_chunks, lo, hi, desc = BATCH_WORKLOADS[args.workload]
+    t_gen = time.time()
+    B = BatchInputs(n_chunks, lo, hi, seed=rank)
+    t_gen = time.time() - t_gen
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    # inputs: every chunk's code window and code_offsets in one device buffer each
+    code_off, co_off = [], []
+    cb = cob = 0
+    for (c, d, b0, b1, co) in B.chunks:
+        code_off.append(cb)
+        cb = _align(cb + (b1 - b0))
+        co_off.append(cob)
+        cob = _align(cob + co.size * 4)
+    h_codes = np.zeros(cb, np.uint8)
+    h_co = np.zeros(cob, np.uint8)
+    for i, (c, d, b0, b1, co) in enumerate(B.chunks):
+        h_codes[code_off[i]:code_off[i] + (b1 - b0)] = B.pools[c].stream[b0:b1]
+        h_co[co_off[i]:co_off[i] + co.size * 4] = co.view(np.uint8)
+    codes = torch.from_numpy(h_codes).to(dev)
+    cos = torch.from_numpy(h_co).to(dev)
+    dicts = [fp.Dict(c, d.data, d.offsets, sh) for (c, d, b0, b1, co) in B.chunks]
+
+    # exact decoded sizes (the library's length pass), then one output buffer
+    totals, out_off, offs_off = [], [], []
+    ob = oob = 0
+    for i, (c, d, b0, b1, co) in enumerate(B.chunks):
+        st, tot = fp.decoded_size(c, dicts[i], codes.data_ptr() + code_off[i], b1 - b0,
+                                  cos.data_ptr() + co_off[i], co.size - 1, sh)
+        if st != fp.OK:
+            raise RuntimeError(f"chunk {i}: {fp.STATUS_NAMES[st]} {fp.last_error()}")
+        totals.append(tot)
+        out_off.append(ob)
+        ob = _align(ob + tot)
+        offs_off.append(oob)
+        oob = _align(oob + co.size * 4)
+    out = torch.empty(max(ob, 256), dtype=torch.uint8, device=dev)
+    offs = torch.empty(max(oob, 256), dtype=torch.uint8, device=dev)
+    chunks = [fp.chunk(c, dicts[i], codes.data_ptr() + code_off[i], b1 - b0, cos.data_ptr() + co_off[i],
+                       co.size - 1, out.data_ptr() + out_off[i], totals[i], offs.data_ptr() + offs_off[i])
+              for i, (c, d, b0, b1, co) in enumerate(B.chunks)]
+    total = int(sum(totals))
+    t_tune = time.time()
+    plan = fp.Plan(chunks, tune_cache=None, stream=sh)
+    t_tune = time.time() - t_tune
+    pinfo = plan.info()
+
+    def step():
+        plan.decode(sh)
+
+    step()
+    st, sts, tot = plan.sync_status(sh)
+    if st != fp.OK or not np.array_equal(tot, np.asarray(totals, np.uint64)):
+        raise RuntimeError(f"batch: {fp.STATUS_NAMES.get(st, st)} {fp.last_error()}")
+
+    gpu_id = str(local_rank)
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id)
+    t_end = time.time() + args.settle
+    while time.time() < t_end:
+        step()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    st, sts, tot = plan.sync_status(sh)
+    if st != fp.OK:
+        raise RuntimeError(fp.last_error())
+    all_bytes = float(total)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        bt = torch.tensor([all_bytes], device=dev, dtype=torch.float64)
+        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+        all_bytes = float(bt.item())
+    value = all_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    avg_s = statistics.mean(launch_ms) * 1e-3
+    alg = 0
+    for i, (c, d, b0, b1, co) in enumerate(B.chunks):
+        used = int(co[-1]) - int(co[0])
+        alg += (used * synth.CODE_BITS[c] + 7) // 8 + 8 * co.size + totals[i] + d.n_entries * (synth.MAX_TOKEN[c] + 1)
+    peak, peak_kind = load_peaks()
+    achieved = alg / avg_s / 1e9
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # one launch (sequence) per chunk: the plain one-thread-per-string decode, and fp_decode
+        def per_chunk(fn):
+            fn(*chunk_args(0))
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            a.record(stream)
+            for _ in range(reps):
+                for i in range(n_chunks):
+                    fn(*chunk_args(i))
+            b.record(stream)
+            torch.cuda.synchronize()
+            if fp.sync_status(sh) != fp.OK:
+                raise RuntimeError(fp.last_error())
+            ms = a.elapsed_time(b) / reps
+            return total / (ms * 1e-3) / 1e9, ms
+
+        def chunk_args(i):
+            c, d, b0, b1, co = B.chunks[i]
+            return (c, dicts[i], codes.data_ptr() + code_off[i], b1 - b0, cos.data_ptr() + co_off[i], co.size - 1,
+                    out.data_ptr() + out_off[i], totals[i], offs.data_ptr() + offs_off[i], sh)
+
+        pg, pms = per_chunk(fp.decode_plain)
+        extra["plain_gpu"] = {"value": round(pg, 2), "unit": "GB/s",
+                              "kind": "one plain launch sequence per chunk (one thread per string)",
+                              "ms": round(pms, 2), "batched_over_plain": round(value / pg, 2)}
+        sg, sms = per_chunk(fp.decode)
+        extra["per_chunk_fp_decode"] = {"value": round(sg, 2), "unit": "GB/s",
+                                        "kind": "one fp_decode (index pass + decode kernel) per chunk",
+                                        "ms": round(sms, 2)}
+
+        # end to end: pinned host inputs in, decoded bytes and offsets out, every step
+        hp_codes = torch.from_numpy(h_codes).pin_memory()
+        hp_co = torch.from_numpy(h_co).pin_memory()
+        hp_out = torch.empty(out.numel(), dtype=torch.uint8).pin_memory()
+        hp_offs = torch.empty(offs.numel(), dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            codes.copy_(hp_codes, non_blocking=True)
+            cos.copy_(hp_co, non_blocking=True)
+            plan.decode(sh)
+            hp_out.copy_(out, non_blocking=True)
+            hp_offs.copy_(offs, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_n = 3
+        a.record(stream)
+        for _ in range(e2e_n):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if plan.sync_status(sh)[0] != fp.OK:
+            raise RuntimeError(fp.last_error())
+        e2e_s = a.elapsed_time(b) * 1e-3 / e2e_n
+        extra["e2e"] = {"value": round(total / e2e_s / 1e9, 3), "unit": "GB/s",
+                        "h2d_bytes_per_step": int(h_codes.size + h_co.size),
+                        "d2h_bytes_per_step": int(out.numel() + offs.numel())}
+        del hp_codes, hp_co, hp_out, hp_offs
+
+        # CPU oracle on the host cores: whole chunks in order, about cpu_seconds of work
+        import oracle
+        threads = os.cpu_count() or 1
+        done_b, t_cpu, k = 0, 0.0, 0
+        while k < n_chunks and t_cpu < args.cpu_seconds:
+            col = B.host_column(k)
+            t = time.perf_counter()
+            r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets,
+                              threads=threads)
+            t_cpu += time.perf_counter() - t
+            done_b += r.total
+            k += 1
+        extra["cpu_baseline"] = {"value": round(done_b / t_cpu / 1e9, 4), "unit": "GB/s", "cores": threads,
+                                 "kind": "oracle", "sample": f"first {k} of {n_chunks} chunks "
+                                                             f"({done_b} decoded bytes), {t_cpu:.1f} s"}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    counts = {synth.CODEC_NAMES[c]: int((B.codecs == c).sum()) for c in (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8)}
+    line = {
+        "metric": BATCH_METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc, "n_chunks": n_chunks, "codec_chunks": counts,
+                   "decoded_bytes": total, "code_bytes": int(sum(b1 - b0 for (_, _, b0, b1, _) in B.chunks)),
+                   "n_strings": int(sum(co.size - 1 for (*_, co) in B.chunks)),
+                   "largest_chunk_bytes": int(max(totals)), "smallest_chunk_bytes": int(min(totals)),
+                   "l2": "inputs and output larger than L2 (no flush needed)",
+                   "plan": pinfo, "generation_s": round(t_gen, 1), "plan_create_s": round(t_tune, 2),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": load_traffic(args.workload), "algorithmic_bytes_per_launch": alg,
+                     "kernel_ms": round(avg_s * 1e3, 4)},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,   # per step: one graph = the index pass and the persistent decode kernel
+    }
+    line.update(extra)
+    if "e2e" not in line:
+        line["e2e"] = None
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_batched_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    n_chunks, lo, hi, desc = BATCH_WORKLOADS[args.workload]
+    B = BatchInputs(n_chunks, lo, hi, seed=0)
+    threads = os.cpu_count() or 1
+    per_step = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
+    vals = []
+    k = 0
+    last = (0, 0, 0.0)
+    for i in range(args.warmup + args.steps):
+        done_b, t_cpu, first = 0, 0.0, k
+        while t_cpu < per_step:
+            col = B.host_column(k % n_chunks)
+            t = time.perf_counter()
+            r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets,
+                              threads=threads)
+            t_cpu += time.perf_counter() - t
+            done_b += r.total
+            k += 1
+        if i >= args.warmup:
+            vals.append(done_b / t_cpu / 1e9)
+            last = (k - first, done_b, t_cpu)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(last[2] * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc, "n_chunks": n_chunks},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{last[0]} whole chunks ({last[1]} decoded bytes) per step"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="onpair12_10m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="onpair12_10m", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed decoding before warm-up")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -377,8 +699,11 @@ def main():
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local_rank = env_rank()
+    batched = args.workload in BATCH_WORKLOADS
     if args.impl == "reference":
-        run_reference(args, rank, world)
+        (run_batched_reference if batched else run_reference)(args, rank, world)
+    elif batched:
+        run_batched(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

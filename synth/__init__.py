@@ -408,3 +408,63 @@ def column(codec: int, seed: int, n_strings: int, **kw) -> Column:
     if codec == FSST8:
         return fsst8_column(seed, n_strings, **kw)
     raise ValueError(codec)
+
+
+# ---------------------------------------------------------------------------
+# Batches of chunks and served requests: many columns, each with its own
+# dictionary, cut from per-codec pools of code streams.  Any code stream is
+# valid under any full dictionary of its codec (every code has a token), so
+# a chunk pairs a window of its codec's pool with its own dictionary.
+# ---------------------------------------------------------------------------
+
+def onpair12_dictionary_variant(base: Dictionary, seed: int) -> Dictionary:
+    """A distinct OnPair-12 dictionary from a base one: the one-byte literals
+    stay at codes 0..255, the multi-byte tokens are permuted over codes
+    256..4095 (seeded)."""
+    rng = rng_for(2, seed, 7)
+    n = base.n_entries
+    idx = np.concatenate([np.arange(256), 256 + rng.permutation(n - 256)])
+    lens = base.token_lengths()[idx]
+    offs = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    src = np.repeat(base.offsets[:-1].astype(np.int64)[idx] - offs[:-1], lens) + np.arange(int(offs[-1]))
+    return Dictionary(ONPAIR12, base.data[src].copy(), offs.astype(np.uint32))
+
+
+def chunk_dictionary(codec: int, seed: int, onpair12_bases=None) -> Dictionary:
+    """The dictionary of chunk `seed`: generated as for the single-column
+    workloads (OnPair-12: a permuted variant of one of a few base
+    dictionaries, which are slow to draw)."""
+    if codec == ONPAIR16:
+        return onpair16_dictionary(seed)
+    if codec == FSST8:
+        return fsst8_dictionary(seed)
+    bases = onpair12_bases if onpair12_bases is not None else [onpair12_dictionary(0)]
+    return onpair12_dictionary_variant(bases[seed % len(bases)], seed)
+
+
+def log_uniform_sizes(rng, n: int, lo: int, hi: int) -> np.ndarray:
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(np.int64)
+
+
+def codec_mix(rng, n: int, ratio=(2, 1, 1)) -> np.ndarray:
+    """Codecs in ratio OnPair-16 : OnPair-12 : FSST-8, shuffled."""
+    r = np.asarray(ratio, np.float64)
+    counts = np.floor(n * r / r.sum()).astype(np.int64)
+    counts[0] += n - counts.sum()
+    codecs = np.repeat(np.array([ONPAIR16, ONPAIR12, FSST8]), counts)
+    return codecs[rng.permutation(n)]
+
+
+def pool_window(pool: Column, start: int, n_strings: int):
+    """Strings [start, start + n) of a pool column as a chunk: the byte range of
+    the pool's stored code buffer that holds them, starting on a 48-byte
+    boundary (a whole number of slots for every codec and 16-byte aligned),
+    and code_offsets rebased to that range.  Returns (byte0, byte1, code_offsets)."""
+    w = CODE_BITS[pool.codec]
+    co = pool.code_offsets[start:start + n_strings + 1].astype(np.int64)
+    first_byte = int(co[0]) * w // 8
+    byte0 = first_byte - first_byte % 48
+    slot0 = byte0 * 8 // w
+    end_byte = (int(co[-1]) * w + 7) // 8
+    return byte0, end_byte, (co - slot0).astype(np.uint32)
