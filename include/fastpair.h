@@ -299,6 +299,97 @@ int fp_batch_config_count(void);
 fp_status fp_batch_config_info(int config, uint32_t* slots_per_thread3, uint32_t* blocks_per_sm);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Served decode (no counterpart API in the paper): a request loop with
+ * continuous batching.  Requests (a column already on the device plus the
+ * key of a registered dictionary) are submitted from any thread; a
+ * scheduler thread inside the library admits them in arrival order while
+ * the bytes in flight stay within an HBM budget, keeps dictionaries in a
+ * device cache, and decodes the admitted requests in waves -- one
+ * persistent batched launch each -- on several streams at once, so requests
+ * arriving while others run start as soon as a stream and memory free up.
+ * Outputs live in a device arena owned by the server until released.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct fp_server fp_server;   /* opaque */
+
+typedef struct fp_serve_config {
+    uint64_t hbm_budget;        /* bytes: outputs (until released) + inputs (until decoded) in flight;
+                                   the output arena of this size is allocated at creation */
+    uint32_t dict_cache_slots;  /* device-resident dictionaries (0 = 512); 1.06 MiB each */
+    uint32_t max_inflight;      /* admitted requests not yet decoded (0 = 4096) */
+    uint32_t n_streams;         /* waves in flight at once (0 = 4) */
+    uint32_t max_wave;          /* requests per wave (0 = 256) */
+    int32_t batch_config;       /* batch configuration of the waves (see fp_batch_config_info) */
+    uint32_t reserved;
+} fp_serve_config;
+
+typedef struct fp_request {
+    uint64_t dict_key;                /* a key registered with fp_serve_dict_put        */
+    const void* d_codes;              /* device, 16-byte aligned, as fp_decode           */
+    uint64_t codes_bytes;
+    const uint32_t* d_code_offsets;   /* device, n_strings + 1                           */
+    uint32_t n_strings;
+    uint32_t reserved;
+    uint64_t decoded_size;            /* exact decoded bytes (column metadata); a smaller
+                                         value fails the request with FP_ERR_CAPACITY     */
+    uint64_t user_tag;                /* returned with the result                        */
+} fp_request;
+
+typedef struct fp_result {
+    uint64_t ticket;
+    uint32_t status;                  /* fp_status of the request                        */
+    uint32_t reserved;
+    uint8_t* d_out_bytes;             /* device, valid until fp_serve_release            */
+    uint32_t* d_out_offsets;          /* device, n_strings + 1                           */
+    uint64_t bytes;                   /* decoded bytes                                   */
+    uint64_t n_strings;
+    int64_t t_submit_ns, t_admit_ns, t_done_ns;   /* host steady clock                   */
+    uint64_t user_tag;
+} fp_result;
+
+typedef struct fp_serve_stats_t {
+    uint64_t submitted, admitted, completed, failed, released;
+    uint64_t waves;
+    uint32_t max_wave_seen;
+    uint32_t queued;                  /* submitted, not yet admitted                     */
+    uint64_t bytes_decoded;
+    uint64_t dict_hits, dict_misses, dict_evictions, dicts_registered;
+    uint64_t inflight_bytes, peak_inflight_bytes;
+    uint32_t inflight_requests;
+    uint32_t reserved;
+} fp_serve_stats_t;
+
+/* Create a server on the current device (allocates the output arena and the
+ * dictionary slots, starts the scheduler thread). */
+fp_status fp_serve_create(const fp_serve_config* config, fp_server** out);
+
+/* Register a dictionary under `key` (validated and repacked on the host at
+ * once; uploaded into a device slot when a request needs it).  Keys are
+ * unique: FP_ERR_ARG if `key` exists. */
+fp_status fp_serve_dict_put(fp_server* server, uint64_t key, fp_codec codec, const uint8_t* h_bytes,
+                            const uint32_t* h_offsets, uint32_t n_entries);
+
+/* Queue a request.  Returns at once with a ticket.  The input buffers must
+ * stay valid and unchanged until the request completes.  FP_ERR_BUSY if the
+ * request alone exceeds the HBM budget or the server is shutting down. */
+fp_status fp_serve_submit(fp_server* server, const fp_request* request, uint64_t* ticket);
+
+/* Take up to `max` completed requests (waiting up to timeout_ns for the
+ * first one).  Each result's outputs stay valid until fp_serve_release. */
+fp_status fp_serve_poll(fp_server* server, fp_result* out, uint32_t max, uint32_t* n, int64_t timeout_ns);
+
+/* Return a polled request's output memory to the server.
+ * FP_ERR_NOT_READY if the request has not completed or not been polled. */
+fp_status fp_serve_release(fp_server* server, uint64_t ticket);
+
+fp_status fp_serve_stats(fp_server* server, fp_serve_stats_t* out);
+
+/* Stop admitting, finish the waves on the GPU, free everything (requests
+ * still queued are dropped). */
+fp_status fp_serve_destroy(fp_server* server);
+
+/*
  * Decode variants (tile shapes).  A variant fixes the threads per block, the
  * code slots each thread decodes and where the dictionary is read from
  * (shared memory staged once per block, or the L1/L2 cache path).

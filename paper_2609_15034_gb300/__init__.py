@@ -71,11 +71,20 @@ def lib() -> ctypes.CDLL:
             L.fp_plan_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
             L.fp_plan_destroy.argtypes = [P]
             L.fp_batch_config_info.argtypes = [I, P, ctypes.POINTER(U32)]
+            L.fp_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]
+            L.fp_serve_dict_put.argtypes = [P, U64, I, P, P, U32]
+            L.fp_serve_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(U64)]
+            L.fp_serve_poll.argtypes = [P, ctypes.POINTER(Result), U32, ctypes.POINTER(U32), ctypes.c_int64]
+            L.fp_serve_release.argtypes = [P, U64]
+            L.fp_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
+            L.fp_serve_destroy.argtypes = [P]
             for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
                          "fp_decode_noalloc",
                          "fp_sync_status", "fp_variant_info", "fp_variant_select",
                          "fp_plan_create", "fp_plan_create_config", "fp_decode_batch", "fp_plan_sync_status",
-                         "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info"):
+                         "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info", "fp_serve_create",
+                         "fp_serve_dict_put", "fp_serve_submit", "fp_serve_poll", "fp_serve_release",
+                         "fp_serve_stats", "fp_serve_destroy"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib
@@ -114,6 +123,35 @@ class PlanInfo(ctypes.Structure):
                 ("grid", ctypes.c_uint32), ("index_blocks", ctypes.c_uint32), ("from_cache", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("total_tiles", ctypes.c_uint64), ("layout_bytes", ctypes.c_uint64),
                 ("tune_ms", ctypes.c_float * 8)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("dict_cache_slots", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("n_streams", ctypes.c_uint32), ("max_wave", ctypes.c_uint32),
+                ("batch_config", ctypes.c_int32), ("reserved", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dict_key", ctypes.c_uint64), ("d_codes", ctypes.c_void_p), ("codes_bytes", ctypes.c_uint64),
+                ("d_code_offsets", ctypes.c_void_p), ("n_strings", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("decoded_size", ctypes.c_uint64), ("user_tag", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("d_out_bytes", ctypes.c_void_p), ("d_out_offsets", ctypes.c_void_p), ("bytes", ctypes.c_uint64),
+                ("n_strings", ctypes.c_uint64), ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64), ("user_tag", ctypes.c_uint64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("released", ctypes.c_uint64), ("waves", ctypes.c_uint64),
+                ("max_wave_seen", ctypes.c_uint32), ("queued", ctypes.c_uint32), ("bytes_decoded", ctypes.c_uint64),
+                ("dict_hits", ctypes.c_uint64), ("dict_misses", ctypes.c_uint64), ("dict_evictions", ctypes.c_uint64),
+                ("dicts_registered", ctypes.c_uint64), ("inflight_bytes", ctypes.c_uint64),
+                ("peak_inflight_bytes", ctypes.c_uint64), ("inflight_requests", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class Dict:
@@ -305,3 +343,94 @@ def batch_config_info(config: int) -> dict:
     _check(lib().fp_batch_config_info(config, ctypes.cast(k, ctypes.c_void_p), ctypes.byref(b)),
            "fp_batch_config_info")
     return {"slots_per_thread": list(k), "blocks_per_sm": b.value}
+
+
+# ---- served decode (fp_serve_*) ----------------------------------------------
+
+class Server:
+    """fp_server: continuous-batching decode loop run by a library thread."""
+
+    def __init__(self, hbm_budget: int, dict_cache_slots: int = 512, max_inflight: int = 4096, n_streams: int = 4,
+                 max_wave: int = 256, batch_config: int = 0):
+        cfg = ServeConfig(hbm_budget, dict_cache_slots, max_inflight, n_streams, max_wave, batch_config, 0)
+        h = ctypes.c_void_p()
+        _check(lib().fp_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "fp_serve_create")
+        self._h = h
+        self._res = (Result * 1024)()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise ValueError("server was destroyed")
+        return self._h
+
+    def dict_put(self, key: int, codec: int, data: np.ndarray, offsets: np.ndarray) -> None:
+        data = np.ascontiguousarray(data, np.uint8)
+        offsets = np.ascontiguousarray(offsets, np.uint32)
+        if data.size == 0:
+            data = np.zeros(1, np.uint8)
+        _check(lib().fp_serve_dict_put(self.handle, key, codec, data.ctypes.data, offsets.ctypes.data,
+                                       offsets.size - 1), "fp_serve_dict_put")
+
+    def submit(self, dict_key: int, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+               decoded_size: int, user_tag: int = 0, check: bool = True):
+        r = Request(dict_key, codes_ptr or None, codes_bytes, code_offsets_ptr, n_strings, 0, decoded_size, user_tag)
+        t = ctypes.c_uint64()
+        st = lib().fp_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        if check:
+            _check(st, "fp_serve_submit")
+            return int(t.value)
+        return st, int(t.value)
+
+    def poll(self, max_results: int = 1024, timeout_s: float = 0.0) -> list:
+        n = ctypes.c_uint32()
+        m = min(max_results, len(self._res))
+        _check(lib().fp_serve_poll(self.handle, self._res, m, ctypes.byref(n), int(timeout_s * 1e9)), "fp_serve_poll")
+        out = []
+        for i in range(n.value):
+            r = self._res[i]
+            out.append({"ticket": r.ticket, "status": r.status, "d_out_bytes": r.d_out_bytes or 0,
+                        "d_out_offsets": r.d_out_offsets or 0, "bytes": r.bytes, "n_strings": r.n_strings,
+                        "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns,
+                        "user_tag": r.user_tag})
+        return out
+
+    def release(self, ticket: int, check: bool = True) -> int:
+        st = lib().fp_serve_release(self.handle, ticket)
+        return _check(st, "fp_serve_release") if check else st
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        _check(lib().fp_serve_stats(self.handle, ctypes.byref(s)), "fp_serve_stats")
+        return {name: getattr(s, name) for name, _ in ServeStats._fields_ if name != "reserved"}
+
+    def destroy(self):
+        if self._h is not None and _lib is not None:
+            _lib.fp_serve_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def device_bytes(ptr: int, n: int):
+    """A torch uint8 view of n bytes of device memory the library owns (for
+    copying a served result out).  Only valid until the result is released."""
+    import torch
+    if n == 0:
+        return torch.empty(0, dtype=torch.uint8, device="cuda")
+    return _DeviceView(ptr, n).tensor()
+
+
+class _DeviceView:
+    def __init__(self, ptr: int, n: int):
+        self.ptr, self.n = ptr, n
+
+    def tensor(self):
+        import torch
+        self.__cuda_array_interface__ = {"shape": (self.n,), "typestr": "|u1", "data": (self.ptr, False),
+                                         "version": 3, "strides": None}
+        return torch.as_tensor(self, device="cuda")

@@ -246,6 +246,32 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
 }
 
 }  // namespace
+
+fp_status repack_dictionary(fp_codec codec, const uint8_t* h_bytes, const uint32_t* h_offsets, uint32_t n_entries,
+                            std::vector<uint8_t>& table, std::vector<uint8_t>& lens, std::vector<uint32_t>& offs) {
+    if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
+    if (!h_offsets || !h_bytes) return fail(FP_ERR_ARG, "h_bytes/h_offsets is NULL");
+    if (n_entries < 1 || n_entries > max_entries(codec))
+        return fail(FP_ERR_ARG, "n_entries %u out of range 1..%u", n_entries, max_entries(codec));
+    const uint32_t L = max_token(codec);
+    for (uint32_t i = 0; i < n_entries; ++i) {
+        if (h_offsets[i + 1] < h_offsets[i]) return fail(FP_ERR_ARG, "h_offsets decrease at %u", i);
+        const uint32_t len = h_offsets[i + 1] - h_offsets[i];
+        if (len < 1 || len > L) return fail(FP_ERR_ARG, "token %u has length %u (allowed 1..%u)", i, len, L);
+    }
+    const uint32_t n_tab = table_entries(codec), stride = table_stride(codec);
+    table.assign((size_t)n_tab * stride, 0);
+    lens.assign(n_tab, 0);
+    for (uint32_t i = 0; i < n_entries; ++i) {
+        const uint32_t a = h_offsets[i], len = h_offsets[i + 1] - a;
+        memcpy(&table[(size_t)i * stride], h_bytes + a, len);
+        lens[i] = (uint8_t)len;
+    }
+    offs.resize(n_entries + 1);
+    for (uint32_t i = 0; i <= n_entries; ++i) offs[i] = h_offsets[i] - h_offsets[0];
+    return FP_OK;
+}
+
 }  // namespace fp
 
 using namespace fp;
@@ -259,26 +285,11 @@ fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t*
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     if (!out) return fail(FP_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
-    if (!h_offsets || !h_bytes) return fail(FP_ERR_ARG, "h_bytes/h_offsets is NULL");
-    if (n_entries < 1 || n_entries > max_entries(codec))
-        return fail(FP_ERR_ARG, "n_entries %u out of range 1..%u", n_entries, max_entries(codec));
-    const uint32_t L = max_token(codec);
-    for (uint32_t i = 0; i < n_entries; ++i) {
-        if (h_offsets[i + 1] < h_offsets[i]) return fail(FP_ERR_ARG, "h_offsets decrease at %u", i);
-        const uint32_t len = h_offsets[i + 1] - h_offsets[i];
-        if (len < 1 || len > L) return fail(FP_ERR_ARG, "token %u has length %u (allowed 1..%u)", i, len, L);
-    }
-    const uint32_t n_tab = table_entries(codec), stride = table_stride(codec);
-    std::vector<uint8_t> table((size_t)n_tab * stride, 0), lens(n_tab, 0);
-    for (uint32_t i = 0; i < n_entries; ++i) {
-        const uint32_t a = h_offsets[i], len = h_offsets[i + 1] - a;
-        memcpy(&table[(size_t)i * stride], h_bytes + a, len);
-        lens[i] = (uint8_t)len;
-    }
-    const uint32_t base = h_offsets[0], nbytes = h_offsets[n_entries] - base;
-    std::vector<uint32_t> offs(n_entries + 1);
-    for (uint32_t i = 0; i <= n_entries; ++i) offs[i] = h_offsets[i] - base;
+    std::vector<uint8_t> table, lens;
+    std::vector<uint32_t> offs;
+    fp_status st = repack_dictionary(codec, h_bytes, h_offsets, n_entries, table, lens, offs);
+    if (st != FP_OK) return st;
+    const uint32_t base = h_offsets[0], nbytes = offs[n_entries];
 
     fp_dict* d = new fp_dict();
     d->codec = codec;

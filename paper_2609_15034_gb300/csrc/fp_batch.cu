@@ -152,32 +152,46 @@ struct fp_plan {
 
 namespace {
 
-// Lay out the device tables of configuration `cfg` and fill the launch
-// parameters; replaces the plan's previous layout.
-fp_status build_layout(fp_plan* P, int cfg) {
-    const Config& C = configs()[cfg];
-    const BatchKernel& BK = batch_kernels()[C.kernel];
-    const uint32_t n = (uint32_t)P->chunks.size();
-    std::vector<uint32_t> qlist[3];
-    for (uint32_t i = 0; i < n; ++i) qlist[P->chunks[i].codec - 1].push_back(i);
+// Host image of a batch's device tables.  The device layout is
+//   chunk records (per queue) | ticket -> chunk (per queue) | index blocks |
+//   tile -> first string (per chunk) | look-back words (per tile);
+// the image holds the first three parts (`table_bytes`); the index pass
+// writes the fourth and the look-back words are tagged per launch.
+struct LayoutImage {
+    std::vector<char> bytes;
+    size_t o_src[3], o_tc[3], o_ib, o_first, o_ts, table_bytes, total_bytes;
+    uint64_t total_tiles = 0;
+    uint32_t n_idx = 0;
+    uint32_t n_tiles_q[3], n_chunks_q[3];
+    uint64_t slots_q[3];
+};
 
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Tables of `n` chunks for batch kernel BK.  Chunk i reports into
+// d_status[i] / d_total[i].  Device addresses inside the records are
+// offsets until relocate() adds the layout's base.
+fp_status make_layout(const fp_chunk* chunks, uint32_t n, const BatchKernel& BK, uint32_t* d_status,
+                      unsigned long long* d_total, WsHeader* ws, LayoutImage& L) {
+    std::vector<uint32_t> qlist[3];
+    for (uint32_t i = 0; i < n; ++i) qlist[chunks[i].codec - 1].push_back(i);
     std::vector<SlotSrc> src[3];
     std::vector<uint32_t> tchunk[3];
     std::vector<IdxBlock> iblk;
     uint64_t tile_glob = 0, first_glob = 0;
-    uint64_t slots_q[3] = {0, 0, 0};
     for (int q = 0; q < 3; ++q) {
         const int codec = q + 1;
         const uint64_t T = (uint64_t)kWork * (uint64_t)BK.k[q];
         uint32_t tile_q = 0;
+        L.slots_q[q] = 0;
         for (uint32_t ci = 0; ci < qlist[q].size(); ++ci) {
             const uint32_t i = qlist[q][ci];
-            const fp_chunk& c = P->chunks[i];
+            const fp_chunk& c = chunks[i];
             const uint64_t ms = max_slots_of(codec, c.codes_bytes);
             uint64_t nt = (ms + T - 1) / T;
             if (nt == 0) nt = 1;
             if ((uint64_t)tile_q + nt > 0x7fffffffull) return fail(FP_ERR_ARG, "batch has too many tiles for one codec");
-            slots_q[q] += ms;
+            L.slots_q[q] += ms;
             SlotSrc s;
             memset(&s, 0, sizeof(s));
             s.p.dict = c.dict->view();
@@ -190,18 +204,17 @@ fp_status build_layout(fp_plan* P, int cfg) {
             s.p.capacity = c.out_capacity;
             s.p.out_offsets = c.d_out_offsets;
             s.p.size_only = 0;
-            // device pointers are filled in below, relative to the layout base
             s.p.tile_status = reinterpret_cast<unsigned long long*>((uintptr_t)tile_glob);
             s.p.first = reinterpret_cast<const uint32_t*>((uintptr_t)first_glob);
-            s.p.err_word = P->d_status + i;
-            s.p.total_out = P->d_total + i;
-            s.p.ws = static_cast<WsHeader*>(P->d_hdr);
+            s.p.err_word = d_status + i;
+            s.p.total_out = d_total + i;
+            s.p.ws = ws;
             s.x.first_tile = 0;
             s.x.n_tiles = nt;
             s.tile_base = tile_q;
             s.chunk = i;
             src[q].push_back(s);
-            for (uint64_t u = 0; u < nt; ++u) tchunk[q].push_back(ci);
+            tchunk[q].insert(tchunk[q].end(), nt, ci);
             const uint64_t nb = (uint64_t)c.n_strings + 1;
             for (uint64_t st = 0; st < nb; st += kIdxPerBlock)
                 iblk.push_back(IdxBlock{((uint32_t)q << 30) | ci, (uint32_t)st});
@@ -209,104 +222,138 @@ fp_status build_layout(fp_plan* P, int cfg) {
             tile_glob += nt;
             first_glob += nt + 1;
         }
+        L.n_tiles_q[q] = tile_q;
+        L.n_chunks_q[q] = (uint32_t)src[q].size();
     }
     if (iblk.size() > 0x7fffffffull) return fail(FP_ERR_ARG, "batch has too many strings");
-
-    // device layout: src[0..2] | tile_chunk[0..2] | idx blocks | first | tile status
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off = 0, o_src[3], o_tc[3];
-    for (int q = 0; q < 3; ++q) { o_src[q] = off; off = al(off + src[q].size() * sizeof(SlotSrc)); }
-    for (int q = 0; q < 3; ++q) { o_tc[q] = off; off = al(off + tchunk[q].size() * sizeof(uint32_t)); }
-    const size_t o_ib = off; off = al(off + iblk.size() * sizeof(IdxBlock));
-    const size_t o_first = off; off = al(off + first_glob * sizeof(uint32_t));
-    const size_t o_ts = off; off = al(off + tile_glob * sizeof(unsigned long long));
-    const size_t bytes = off;
-
-    if (P->d_layout) {
-        cudaFree(P->d_layout);
-        P->d_layout = nullptr;
-    }
-    cudaError_t e = cudaMalloc(&P->d_layout, bytes);
-    if (e != cudaSuccess) { P->d_layout = nullptr; return cuda_fail(e, "cudaMalloc(batch layout)"); }
-    char* base = static_cast<char*>(P->d_layout);
-    for (int q = 0; q < 3; ++q)
-        for (SlotSrc& s : src[q]) {
-            s.p.tile_status = reinterpret_cast<unsigned long long*>(base + o_ts) + (uintptr_t)s.p.tile_status;
-            s.p.first = reinterpret_cast<const uint32_t*>(base + o_first) + (uintptr_t)s.p.first;
-        }
-    std::vector<char> host(bytes, 0);
+    size_t off = 0;
+    for (int q = 0; q < 3; ++q) { L.o_src[q] = off; off = align256(off + src[q].size() * sizeof(SlotSrc)); }
+    for (int q = 0; q < 3; ++q) { L.o_tc[q] = off; off = align256(off + tchunk[q].size() * sizeof(uint32_t)); }
+    L.o_ib = off; off = align256(off + iblk.size() * sizeof(IdxBlock));
+    L.table_bytes = off;
+    L.o_first = off; off = align256(off + first_glob * sizeof(uint32_t));
+    L.o_ts = off; off = align256(off + tile_glob * sizeof(unsigned long long));
+    L.total_bytes = off;
+    L.total_tiles = tile_glob;
+    L.n_idx = (uint32_t)iblk.size();
+    L.bytes.assign(L.table_bytes, 0);
     for (int q = 0; q < 3; ++q) {
-        if (!src[q].empty()) memcpy(&host[o_src[q]], src[q].data(), src[q].size() * sizeof(SlotSrc));
-        if (!tchunk[q].empty()) memcpy(&host[o_tc[q]], tchunk[q].data(), tchunk[q].size() * sizeof(uint32_t));
+        if (!src[q].empty()) memcpy(&L.bytes[L.o_src[q]], src[q].data(), src[q].size() * sizeof(SlotSrc));
+        if (!tchunk[q].empty()) memcpy(&L.bytes[L.o_tc[q]], tchunk[q].data(), tchunk[q].size() * sizeof(uint32_t));
     }
-    memcpy(&host[o_ib], iblk.data(), iblk.size() * sizeof(IdxBlock));
-    e = cudaMemcpy(base, host.data(), bytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(batch layout)");
+    if (!iblk.empty()) memcpy(&L.bytes[L.o_ib], iblk.data(), iblk.size() * sizeof(IdxBlock));
+    return FP_OK;
+}
 
-    // launch width: blocks that fit, at most the configuration's per-SM count
-    e = cudaFuncSetAttribute(BK.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BK.smem_bytes);
+// Turn the records' offsets into addresses of a layout placed at `base`.
+void relocate(LayoutImage& L, char* base) {
+    for (int q = 0; q < 3; ++q) {
+        SlotSrc* s = reinterpret_cast<SlotSrc*>(&L.bytes[L.o_src[q]]);
+        for (uint32_t c = 0; c < L.n_chunks_q[q]; ++c) {
+            s[c].p.tile_status = reinterpret_cast<unsigned long long*>(base + L.o_ts) + (uintptr_t)s[c].p.tile_status;
+            s[c].p.first = reinterpret_cast<const uint32_t*>(base + L.o_first) + (uintptr_t)s[c].p.first;
+        }
+    }
+}
+
+// Blocks of the persistent launch: those that fit, at most `bps` per SM,
+// spread over the queues in proportion to their code slots.
+fp_status launch_shape(const LayoutImage& L, const BatchKernel& BK, int bps_limit, int sms, int* grid_out,
+                       uint32_t split[2]) {
+    cudaError_t e = cudaFuncSetAttribute(BK.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BK.smem_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batch)");
     int fit = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, BK.kernel, kThreads, BK.smem_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)");
     if (fit < 1) return fail(FP_ERR_CUDA, "batch kernel does not fit on an SM");
-    const int bps = std::min(fit, C.bps);
-    uint64_t grid = (uint64_t)bps * (uint64_t)P->sms;
-    if (grid > tile_glob) grid = tile_glob;
+    const int bps = std::min(fit, bps_limit);
+    uint64_t grid = (uint64_t)bps * (uint64_t)sms;
+    if (grid > L.total_tiles) grid = L.total_tiles;
     if (grid < 1) grid = 1;
-
-    BatchParams bp;
-    memset(&bp, 0, sizeof(bp));
-    bp.ws = static_cast<WsHeader*>(P->d_hdr);
-    for (int q = 0; q < 3; ++q) {
-        bp.q[q].src = reinterpret_cast<const SlotSrc*>(base + o_src[q]);
-        bp.q[q].tile_chunk = reinterpret_cast<const uint32_t*>(base + o_tc[q]);
-        bp.q[q].n_tiles = (uint32_t)tchunk[q].size();
-        bp.q[q].n_chunks = (uint32_t)src[q].size();
-    }
-    // starting queues in proportion to code slots (at least one block per non-empty queue)
-    const double tot = (double)(slots_q[0] + slots_q[1] + slots_q[2]) + 1e-9;
+    const double tot = (double)(L.slots_q[0] + L.slots_q[1] + L.slots_q[2]) + 1e-9;
     uint32_t g[3];
-    uint32_t left = (uint32_t)grid;
     for (int q = 0; q < 3; ++q) {
-        g[q] = bp.q[q].n_tiles ? (uint32_t)std::floor((double)grid * (double)slots_q[q] / tot) : 0u;
-        if (bp.q[q].n_tiles && g[q] == 0) g[q] = 1;
+        g[q] = L.n_tiles_q[q] ? (uint32_t)std::floor((double)grid * (double)L.slots_q[q] / tot) : 0u;
+        if (L.n_tiles_q[q] && g[q] == 0) g[q] = 1;
     }
-    while (g[0] + g[1] + g[2] > left) {
+    while (g[0] + g[1] + g[2] > (uint32_t)grid) {
         int m = 0;
         for (int q = 1; q < 3; ++q) if (g[q] > g[m]) m = q;
         --g[m];
     }
-    g[2] = left - g[0] - g[1];
-    bp.split[0] = g[0];
-    bp.split[1] = g[0] + g[1];
+    g[2] = (uint32_t)grid - g[0] - g[1];
+    split[0] = g[0];
+    split[1] = g[0] + g[1];
+    *grid_out = (int)grid;
+    return FP_OK;
+}
 
-    IdxParams ip;
-    memset(&ip, 0, sizeof(ip));
-    ip.blocks = reinterpret_cast<const IdxBlock*>(base + o_ib);
+void make_params(const LayoutImage& L, const BatchKernel& BK, char* base, WsHeader* ws, const uint32_t split[2],
+                 BatchParams& bp, IdxParams& ip) {
+    memset(&bp, 0, sizeof(bp));
+    bp.ws = ws;
     for (int q = 0; q < 3; ++q) {
-        ip.src[q] = reinterpret_cast<SlotSrc*>(base + o_src[q]);
+        bp.q[q].src = reinterpret_cast<const SlotSrc*>(base + L.o_src[q]);
+        bp.q[q].tile_chunk = reinterpret_cast<const uint32_t*>(base + L.o_tc[q]);
+        bp.q[q].n_tiles = L.n_tiles_q[q];
+        bp.q[q].n_chunks = L.n_chunks_q[q];
+    }
+    bp.split[0] = split[0];
+    bp.split[1] = split[1];
+    memset(&ip, 0, sizeof(ip));
+    ip.blocks = reinterpret_cast<const IdxBlock*>(base + L.o_ib);
+    for (int q = 0; q < 3; ++q) {
+        ip.src[q] = reinterpret_cast<SlotSrc*>(base + L.o_src[q]);
         ip.tile[q] = (u32)(kWork * BK.k[q]);
     }
+}
+
+cudaError_t launch_kernels(const BatchKernel& BK, const BatchParams& bp, const IdxParams& ip, uint32_t n_idx, int grid,
+                           cudaStream_t stream) {
+    void* iargs[] = {(void*)&ip};
+    cudaError_t e = cudaLaunchKernel((const void*)&batch_index_kernel, dim3(n_idx), dim3(256), iargs, 0, stream);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&bp};
+    return cudaLaunchKernel(BK.kernel, dim3(grid), dim3(kThreads), args, BK.smem_bytes, stream);
+}
+
+// Lay out configuration `cfg` for a plan (fresh device memory, zeroed
+// look-back words) and fill its launch parameters.
+fp_status build_layout(fp_plan* P, int cfg) {
+    const Config& C = configs()[cfg];
+    const BatchKernel& BK = batch_kernels()[C.kernel];
+    LayoutImage L;
+    fp_status st = make_layout(P->chunks.data(), (uint32_t)P->chunks.size(), BK, P->d_status, P->d_total,
+                               static_cast<WsHeader*>(P->d_hdr), L);
+    if (st != FP_OK) return st;
+    if (P->d_layout) {
+        cudaFree(P->d_layout);
+        P->d_layout = nullptr;
+    }
+    cudaError_t e = cudaMalloc(&P->d_layout, L.total_bytes);
+    if (e != cudaSuccess) { P->d_layout = nullptr; return cuda_fail(e, "cudaMalloc(batch layout)"); }
+    char* base = static_cast<char*>(P->d_layout);
+    relocate(L, base);
+    e = cudaMemcpy(base, L.bytes.data(), L.table_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(base + L.table_bytes, 0, L.total_bytes - L.table_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "batch layout upload");
+    uint32_t split[2];
+    int grid = 0;
+    st = launch_shape(L, BK, C.bps, P->sms, &grid, split);
+    if (st != FP_OK) return st;
+    make_params(L, BK, base, static_cast<WsHeader*>(P->d_hdr), split, P->bp, P->ip);
     P->config = cfg;
-    P->layout_bytes = bytes;
-    P->total_tiles = tile_glob;
-    P->n_idx_blocks = (uint32_t)iblk.size();
-    P->grid = (int)grid;
-    P->bp = bp;
-    P->ip = ip;
-    P->d_tile_status = reinterpret_cast<unsigned long long*>(base + o_ts);
+    P->layout_bytes = L.total_bytes;
+    P->total_tiles = L.total_tiles;
+    P->n_idx_blocks = L.n_idx;
+    P->grid = grid;
+    P->d_tile_status = reinterpret_cast<unsigned long long*>(base + L.o_ts);
     return FP_OK;
 }
 
 cudaError_t launch_batch(const fp_plan* P, cudaStream_t stream) {
     const BatchKernel& BK = batch_kernels()[configs()[P->config].kernel];
-    void* iargs[] = {(void*)&P->ip};
-    cudaError_t e = cudaLaunchKernel((const void*)&batch_index_kernel, dim3(P->n_idx_blocks), dim3(256), iargs, 0,
-                                     stream);
-    if (e != cudaSuccess) return e;
-    void* args[] = {(void*)&P->bp};
-    return cudaLaunchKernel(BK.kernel, dim3(P->grid), dim3(kThreads), args, BK.smem_bytes, stream);
+    return launch_kernels(BK, P->bp, P->ip, P->n_idx_blocks, P->grid, stream);
 }
 
 // Signature of a plan's size mix for the tuning cache: the number of SMs and
@@ -475,6 +522,115 @@ fp_status plan_create(const fp_chunk* chunks, uint32_t n, int force_cfg, const c
 }
 
 }  // namespace
+
+namespace fp {
+
+int batch_config_default() { return 0; }
+
+fp_status wave_init(WaveBuffers& W, uint32_t cap_chunks) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&W.sms, cudaDevAttrMultiProcessorCount, dev);
+    W.cap_chunks = cap_chunks;
+    const size_t o_total = (kWsHeaderBytes + cap_chunks * sizeof(uint32_t) + 7) & ~(size_t)7;
+    const size_t hdr = o_total + (size_t)cap_chunks * sizeof(unsigned long long);
+    if (e == cudaSuccess) e = cudaMalloc(&W.d_hdr, hdr);
+    if (e == cudaSuccess) e = cudaMemset(W.d_hdr, 0, hdr);
+    if (e == cudaSuccess) {
+        const unsigned one = 1;   // launch tag 0 means "never written"
+        e = cudaMemcpy(static_cast<char*>(W.d_hdr) + offsetof(WsHeader, epoch), &one, sizeof(one),
+                       cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&W.h_status), cap_chunks * sizeof(uint32_t) + 64, 0);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void**>(&W.h_total), cap_chunks * sizeof(unsigned long long), 0);
+    if (e != cudaSuccess) {
+        wave_free(W);
+        return cuda_fail(e, "wave buffers");
+    }
+    W.h_ws_status = W.h_status + cap_chunks;
+    W.d_status = reinterpret_cast<uint32_t*>(static_cast<char*>(W.d_hdr) + kWsHeaderBytes);
+    W.d_total = reinterpret_cast<unsigned long long*>(static_cast<char*>(W.d_hdr) + o_total);
+    return FP_OK;
+}
+
+void wave_free(WaveBuffers& W) {
+    if (W.d_hdr) cudaFree(W.d_hdr);
+    if (W.d_layout) cudaFree(W.d_layout);
+    if (W.h_stage) cudaFreeHost(W.h_stage);
+    if (W.h_status) cudaFreeHost(W.h_status);
+    if (W.h_total) cudaFreeHost(W.h_total);
+    W = WaveBuffers();
+}
+
+fp_status wave_launch(WaveBuffers& W, const fp_chunk* chunks, uint32_t n, int config, cudaStream_t stream) {
+    if (n == 0 || n > W.cap_chunks) return fail(FP_ERR_ARG, "wave of %u chunks (capacity %u)", n, W.cap_chunks);
+    const Config& C = configs()[config];
+    const BatchKernel& BK = batch_kernels()[C.kernel];
+    LayoutImage L;
+    WsHeader* ws = static_cast<WsHeader*>(W.d_hdr);
+    fp_status st = make_layout(chunks, n, BK, W.d_status, W.d_total, ws, L);
+    if (st != FP_OK) return st;
+    cudaError_t e;
+    if (L.total_bytes > W.layout_cap) {
+        // grow (the only allocation of a wave; stream-ordered frees would race the previous wave)
+        e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess && W.d_layout) e = cudaFree(W.d_layout);
+        W.d_layout = nullptr;
+        W.layout_cap = 0;
+        size_t cap = 1u << 20;
+        while (cap < L.total_bytes) cap *= 2;
+        if (e == cudaSuccess) e = cudaMalloc(&W.d_layout, cap);
+        if (e == cudaSuccess) e = cudaMemset(W.d_layout, 0, cap);
+        if (e != cudaSuccess) { W.d_layout = nullptr; return cuda_fail(e, "wave layout"); }
+        W.layout_cap = cap;
+    }
+    if (L.table_bytes > W.stage_cap) {
+        if (W.h_stage) cudaFreeHost(W.h_stage);
+        W.h_stage = nullptr;
+        W.stage_cap = 0;
+        size_t cap = 1u << 16;
+        while (cap < L.table_bytes) cap *= 2;
+        e = cudaHostAlloc(&W.h_stage, cap, 0);
+        if (e != cudaSuccess) { W.h_stage = nullptr; return cuda_fail(e, "wave staging"); }
+        W.stage_cap = cap;
+    }
+    char* base = static_cast<char*>(W.d_layout);
+    relocate(L, base);
+    memcpy(W.h_stage, L.bytes.data(), L.table_bytes);
+    if ((++W.launches & ((1ull << 25) - 1)) == 0) {
+        // look-back words carry a 26-bit launch tag; clear them well before it wraps
+        e = cudaMemsetAsync(base, 0, W.layout_cap, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "wave status clear");
+    }
+    e = cudaMemcpyAsync(base, W.h_stage, L.table_bytes, cudaMemcpyHostToDevice, stream);
+    // the look-back words move with the table sizes: clear them, so that no
+    // earlier wave's table bytes can pass for a published word
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.o_ts, 0, L.total_tiles * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(W.d_status, 0, n * sizeof(uint32_t), stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(static_cast<char*>(W.d_hdr) + offsetof(WsHeader, status), 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wave upload");
+    uint32_t split[2];
+    int grid = 0;
+    st = launch_shape(L, BK, C.bps, W.sms, &grid, split);
+    if (st != FP_OK) return st;
+    BatchParams bp;
+    IdxParams ip;
+    make_params(L, BK, base, ws, split, bp, ip);
+    e = launch_kernels(BK, bp, ip, L.n_idx, grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wave launch");
+    e = cudaMemcpyAsync(W.h_status, W.d_status, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(W.h_total, W.d_total, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(W.h_ws_status, static_cast<char*>(W.d_hdr) + offsetof(WsHeader, status), sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wave results");
+    return FP_OK;
+}
+
+}  // namespace fp
 
 extern "C" {
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "fastpair.h"
@@ -120,6 +121,33 @@ cudaError_t launch_plain(int codec, const DecodeParams& p, uint32_t* d_scratch, 
                          cudaStream_t stream);
 size_t plain_scratch_words(uint32_t n_strings);
 
+// A launch slot for batches built on the fly (the server's waves): device
+// header and tables that grow on demand and are otherwise reused, pinned
+// staging for the tables and for the per-chunk results (fp_batch.cu).
+struct WaveBuffers {
+    int sms = 0;
+    uint32_t cap_chunks = 0;
+    void* d_hdr = nullptr;                   // WsHeader | status u32[cap] | total u64[cap]
+    uint32_t* d_status = nullptr;
+    unsigned long long* d_total = nullptr;
+    void* d_layout = nullptr;
+    size_t layout_cap = 0;
+    void* h_stage = nullptr;                 // pinned copy of the tables of the wave in flight
+    size_t stage_cap = 0;
+    uint32_t* h_status = nullptr;            // pinned: the last wave's per-chunk data-error bits
+    unsigned long long* h_total = nullptr;   // pinned: the last wave's per-chunk decoded sizes
+    uint32_t* h_ws_status = nullptr;         // pinned: the last wave's launch-wide bits (timeouts)
+    uint64_t launches = 0;
+};
+fp_status wave_init(WaveBuffers& W, uint32_t cap_chunks);
+void wave_free(WaveBuffers& W);
+// Enqueue the decode of `n` chunks on `stream`: upload the tables, clear
+// the per-chunk words, index pass + persistent decode, then copy the
+// per-chunk results into W.h_status / W.h_total.  The previous wave of W
+// must have completed (its staging is reused).
+fp_status wave_launch(WaveBuffers& W, const fp_chunk* chunks, uint32_t n, int config, cudaStream_t stream);
+int batch_config_default();
+
 // Host helpers (fp_api.cu).
 fp_status fail(fp_status st, const char* fmt, ...);          // sets fp_last_error()
 fp_status cuda_fail(cudaError_t e, const char* what);
@@ -130,6 +158,10 @@ fp_status check_common(fp_codec codec, const fp_dict* dict, const void* d_codes,
                        uint32_t* d_out_offsets, bool need_out);
 fp_status status_from_bits(uint32_t bits);                    // with an fp_last_error() text
 fp_status status_code(uint32_t bits);                         // without
+// Validate a dictionary (interchange form) and repack it into the device
+// layout: fixed-stride table, per-code lengths, offsets rebased to 0.
+fp_status repack_dictionary(fp_codec codec, const uint8_t* h_bytes, const uint32_t* h_offsets, uint32_t n_entries,
+                            std::vector<uint8_t>& table, std::vector<uint8_t>& lens, std::vector<uint32_t>& offs);
 
 inline uint32_t code_bits(int codec) {
     return codec == FP_ONPAIR16 ? 16u : codec == FP_ONPAIR12 ? 12u : codec == FP_FSST8 ? 8u : 0u;
