@@ -43,7 +43,15 @@ BATCH_WORKLOADS = {
                           "4,096 chunks, OnPair-16/OnPair-12/FSST-8 2:1:1, one dictionary each, decoded sizes "
                           "log-uniform 4 KB-16 MB, one persistent launch (CUDA graph)"),
 }
+# served workloads: name -> (arrivals/s, seconds, smallest and largest decoded request, dictionary keys,
+#                             HBM budget, description)
+SERVE_WORKLOADS = {
+    "served": (2000.0, 60.0, 64 << 10, 256 << 20, 512, 40 << 30,
+               "Poisson arrivals at 2,000 requests/s, mixed-codec pages (2:1:1) of 64 KB-256 MB decoded "
+               "(log-uniform), dictionaries Zipf(1.0) over 512 keys in a 512-slot device cache, 40 GB HBM budget"),
+}
 METRIC = "decoded GB/s (single-column decode, inputs resident in HBM)"
+SERVE_METRIC = "served decode: aggregate decoded GB/s at the offered load, with p50/p99 latency"
 BATCH_METRIC = "decoded GB/s (batched decode of many chunks, inputs resident in HBM)"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -682,12 +690,382 @@ def run_batched_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Served decode
+# ---------------------------------------------------------------------------
+
+SERVE_POOL_STRINGS = {synth.ONPAIR16: 2_600_000, synth.ONPAIR12: 2_500_000, synth.FSST8: 5_800_000}
+PAGES_PER_CODEC = 64
+
+
+class ServeInputs:
+    """Pages (columns cut from per-codec pools, decoded sizes log-uniform),
+    dictionary keys (each a dictionary of its codec's length profile, so a
+    page's decoded size is the same under every key of its codec) and a
+    Poisson request stream."""
+
+    def __init__(self, rate, seconds, lo, hi, n_keys, seed=0, n_requests=None):
+        rng = synth.rng_for(6, seed, 0)
+        codecs = (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8)
+        self.pools = {c: synth.column(c, 2000 + seed, SERVE_POOL_STRINGS[c]) for c in codecs}
+        self.pages = {c: [] for c in codecs}   # (byte0, byte1, code_offsets, decoded bytes)
+        for c in codecs:
+            pool = self.pools[c]
+            cum = np.zeros(pool.n_slots + 1, np.int64)
+            np.cumsum(synth.slot_bytes(pool), out=cum[1:])
+            per_string = cum[-1] / pool.n_strings
+            for t in synth.log_uniform_sizes(rng, PAGES_PER_CODEC, lo, hi):
+                n = int(max(1, min(pool.n_strings, round(t / per_string))))
+                start = int(rng.integers(0, pool.n_strings - n + 1))
+                b0, b1, co = synth.pool_window(pool, start, n)
+                a, b = int(pool.code_offsets[start]), int(pool.code_offsets[start + n])
+                self.pages[c].append((b0, b1, co, int(cum[b] - cum[a])))
+        key_codecs = synth.codec_mix(synth.rng_for(6, seed, 1), n_keys)
+        self.keys = [(k, int(key_codecs[k])) for k in range(n_keys)]
+        self.key_dicts = {}
+        rank_to_key = rng.permutation(n_keys)
+        cdf = synth.zipf_cdf(n_keys, 1.0)
+        if n_requests is None:
+            n_requests = int(rate * seconds * 1.2) + 16
+        gaps = rng.exponential(1.0 / rate, n_requests)
+        self.arrivals = np.cumsum(gaps)
+        if n_requests and seconds:
+            self.arrivals = self.arrivals[self.arrivals < seconds]
+        n_req = self.arrivals.size
+        self.req_key = rank_to_key[synth.zipf_draw(rng, cdf, n_req)]
+        self.req_page = rng.integers(0, PAGES_PER_CODEC, n_req)
+
+    def dictionary(self, key):
+        if key not in self.key_dicts:
+            codec = self.keys[key][1]
+            self.key_dicts[key] = synth.same_shape_dictionary(self.pools[codec].dictionary, 7000 + key)
+        return self.key_dicts[key]
+
+    def request(self, i):
+        key = int(self.req_key[i])
+        codec = self.keys[key][1]
+        return key, codec, int(self.req_page[i])
+
+    def host_column(self, key, codec, page):
+        b0, b1, co, _ = self.pages[codec][page]
+        return synth.Column(codec, self.dictionary(key), self.pools[codec].stream[b0:b1], co,
+                            (b1 - b0) * 8 // synth.CODE_BITS[codec])
+
+
+def _progress(msg):
+    sys.stderr.write(f"[{time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
+
+
+def run_served(args, rank, world, local_rank):
+    import faulthandler
+    import threading
+    import torch
+    import paper_2609_15034_gb300 as fp
+
+    faulthandler.dump_traceback_later(args.serve_watchdog, repeat=True)   # thread stacks if a phase hangs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rate, seconds, lo, hi, n_keys, budget, desc = SERVE_WORKLOADS[args.workload]
+    if args.serve_seconds:
+        seconds = args.serve_seconds
+    t_gen = time.time()
+    I = ServeInputs(rate, seconds, lo, hi, n_keys, seed=rank)
+    for k in range(n_keys):
+        I.dictionary(k)
+    t_gen = time.time() - t_gen
+    _progress(f"served: inputs generated in {t_gen:.1f} s, {I.arrivals.size} requests")
+    codecs = (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8)
+    # pages on the device: one buffer for codes, one for code_offsets
+    page_dev = {}
+    for c in codecs:
+        for j, (b0, b1, co, dec) in enumerate(I.pages[c]):
+            codes = torch.from_numpy(np.ascontiguousarray(I.pools[c].stream[b0:b1])).to(dev)
+            cot = torch.from_numpy(co.view(np.int32)).to(dev)
+            page_dev[(c, j)] = (codes, cot, b1 - b0, co.size - 1, dec)
+    srv = fp.Server(hbm_budget=budget, dict_cache_slots=512, n_streams=args.serve_streams,
+                    max_wave=args.serve_wave, batch_config=0)
+    for k, c in I.keys:
+        d = I.dictionary(k)
+        srv.dict_put(k, c, d.data, d.offsets)
+    _progress("served: server up, dictionaries registered")
+
+    def submit(i, tag):
+        key, c, pg = I.request(i)
+        codes, cot, nbytes, n, dec = page_dev[(c, pg)]
+        return srv.submit(key, codes.data_ptr(), nbytes, cot.data_ptr(), n, dec, tag)
+
+    lat, sizes, done_t = [], [], []
+    errors = []
+
+    def consume(n_expected, keep=None):
+        got = 0
+        last = time.time()
+        while got < n_expected:
+            if time.time() - last > args.serve_stall:
+                _progress(f"served: no result for {args.serve_stall} s; {got} of {n_expected}; stats {srv.stats()}")
+                raise RuntimeError("served decode stalled")
+            res = srv.poll(timeout_s=0.05)
+            if res:
+                last = time.time()
+            for r in res:
+                if r["status"] != fp.OK:
+                    errors.append((r["ticket"], r["status"]))
+                if keep is not None and r["user_tag"] in keep:
+                    keep[r["user_tag"]] = fp.device_bytes(r["d_out_bytes"], r["bytes"]).clone()
+                    torch.cuda.current_stream().synchronize()   # copied before the memory is released
+                lat.append((r["t_done_ns"] - r["t_submit_ns"]) * 1e-6)
+                sizes.append(r["bytes"])
+                done_t.append(r["t_done_ns"])
+                srv.release(r["ticket"])
+                got += 1
+
+    # warm-up: every key once (fills the dictionary cache), untimed
+    warm = min(len(I.req_key), 64)
+    for i in range(warm):
+        submit(i, 0)
+    consume(warm)
+    lat.clear(); sizes.clear(); done_t.clear()
+    st0 = srv.stats()
+    _progress(f"served: warm-up done, stats {st0}")
+
+    # open loop: Poisson arrivals; a sample of results is kept to cross-check
+    n_req = int(I.arrivals.size)
+    rs = np.random.default_rng(5)
+    sample = {int(i): None for i in rs.choice(n_req, size=min(12, n_req), replace=False)}
+    cons = threading.Thread(target=consume, args=(n_req, sample))
+    gpu_id = str(local_rank)
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id)
+    cons.start()
+    t_start = time.perf_counter()
+    t0_ns = time.monotonic_ns()
+    late = 0
+    for i in range(n_req):
+        now = time.perf_counter() - t_start
+        wait = I.arrivals[i] - now
+        if wait > 0:
+            time.sleep(wait)
+        elif wait < -0.001:
+            late += 1
+        submit(i, i)
+    cons.join()
+    clocks = sampler.stop()
+    st1 = srv.stats()
+    _progress(f"served: open loop done, stats {st1}")
+    span_s = (max(done_t) - t0_ns) * 1e-9
+    tot_bytes = int(sum(sizes))
+    value = tot_bytes / span_s / 1e9
+    la = np.asarray(lat)
+    if errors:
+        raise RuntimeError(f"served requests failed: {errors[:5]}")
+
+    # cross-check the sampled results against fp_decode of the same page and dictionary
+    dicts = {}
+    for i, out in sample.items():
+        key, c, pg = I.request(i)
+        codes, cot, nbytes, n, dec = page_dev[(c, pg)]
+        if key not in dicts:
+            d = I.dictionary(key)
+            dicts[key] = fp.Dict(c, d.data, d.offsets)
+        ref = torch.empty(dec, dtype=torch.uint8, device=dev)
+        offs = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        fp.decode_tensors(c, dicts[key], codes[:nbytes], cot, n, ref, offs)
+        if fp.sync_status() != fp.OK or not torch.equal(ref, out):
+            raise RuntimeError(f"served request {i} differs from fp_decode")
+
+    extra = {}
+    if not args.quick:
+        # closed loop at saturation: the same request mix, all queued at once
+        n_sat = min(n_req, args.serve_saturation)
+        lat_keep = (list(lat), list(sizes), list(done_t))
+        lat.clear(); sizes.clear(); done_t.clear()
+        cons = threading.Thread(target=consume, args=(n_sat,))
+        cons.start()
+        t0 = time.monotonic_ns()
+        for i in range(n_sat):
+            submit(i, i)
+        cons.join()
+        sat_s = (max(done_t) - t0) * 1e-9
+        _progress("served: saturation run done")
+        sat_bytes = int(sum(sizes))
+        sat_gbs = sat_bytes / sat_s / 1e9
+        lat[:], sizes[:], done_t[:] = lat_keep
+
+        # the same requests, one plain decode (one thread per string) per request, then one fp_decode per request
+        for k, c in I.keys:
+            if k not in dicts:
+                d = I.dictionary(k)
+                dicts[k] = fp.Dict(c, d.data, d.offsets)
+        big = max(v[4] for v in page_dev.values())
+        nmax = max(v[3] for v in page_dev.values())
+        out = torch.empty(big + 16, dtype=torch.uint8, device=dev)
+        offs = torch.empty(nmax + 1, dtype=torch.int32, device=dev)
+        sh = torch.cuda.current_stream().cuda_stream
+
+        def per_request(fn, count):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nb = 0
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            a.record()
+            for i in range(count):
+                key, c, pg = I.request(i)
+                codes, cot, nbytes, n, dec = page_dev[(c, pg)]
+                fn(c, dicts[key], codes.data_ptr(), nbytes, cot.data_ptr(), n, out.data_ptr(), dec, offs.data_ptr(), sh)
+                nb += dec
+            b.record()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t
+            if fp.sync_status(sh) != fp.OK:
+                raise RuntimeError(fp.last_error())
+            return nb / max(a.elapsed_time(b) * 1e-3, wall) / 1e9
+
+        n_plain = min(n_sat, args.serve_plain)
+        plain_gbs = per_request(fp.decode_plain, n_plain)
+        single_gbs = per_request(fp.decode, n_plain)
+        _progress("served: per-request baselines done")
+        extra["saturation"] = {"requests": n_sat, "served_gbs": round(sat_gbs, 2),
+                               "plain_per_request_gbs": round(plain_gbs, 2),
+                               "fp_decode_per_request_gbs": round(single_gbs, 2),
+                               "served_over_plain": round(sat_gbs / plain_gbs, 2),
+                               "plain_requests": n_plain}
+        extra["plain_gpu"] = {"value": round(plain_gbs, 2), "unit": "GB/s",
+                              "kind": "one plain decode (one thread per string) per request, back to back"}
+
+        # end to end: host pages in, decoded bytes out, per request (closed loop)
+        n_e2e = min(n_req, 200)
+        host_in = {}
+        for i in range(n_e2e):
+            key, c, pg = I.request(i)
+            if (c, pg) not in host_in:
+                codes, cot, nbytes, n, dec = page_dev[(c, pg)]
+                host_in[(c, pg)] = (codes.cpu().pin_memory(), cot.cpu().pin_memory())
+        e2e_codes = {k: torch.empty_like(v[0], device=dev) for k, v in host_in.items()}
+        e2e_co = {k: torch.empty_like(v[1], device=dev) for k, v in host_in.items()}
+        h_out = torch.empty(big + 16, dtype=torch.uint8).pin_memory()
+        h2d = d2h = 0
+        t = time.perf_counter()
+        tickets = []
+        nb = 0
+        for i in range(n_e2e):
+            key, c, pg = I.request(i)
+            codes, cot, nbytes, n, dec = page_dev[(c, pg)]
+            hc, hco = host_in[(c, pg)]
+            e2e_codes[(c, pg)].copy_(hc, non_blocking=True)
+            e2e_co[(c, pg)].copy_(hco, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            h2d += hc.numel() + hco.numel() * 4
+            tk = srv.submit(key, e2e_codes[(c, pg)].data_ptr(), nbytes, e2e_co[(c, pg)].data_ptr(), n, dec, i)
+            r = None
+            while r is None:
+                for x in srv.poll(timeout_s=0.05):
+                    r = x
+            h_out[:r["bytes"]].copy_(fp.device_bytes(r["d_out_bytes"], r["bytes"]))
+            d2h += r["bytes"]
+            nb += r["bytes"]
+            srv.release(r["ticket"])
+        e2e_s = time.perf_counter() - t
+        _progress("served: end-to-end leg done")
+        extra["e2e"] = {"value": round(nb / e2e_s / 1e9, 3), "unit": "GB/s",
+                        "h2d_bytes_per_step": int(h2d / n_e2e), "d2h_bytes_per_step": int(d2h / n_e2e),
+                        "kind": f"{n_e2e} requests one at a time: pinned host page -> device, serve, result -> host"}
+
+        # CPU oracle on the host cores, whole requests in arrival order
+        import oracle
+        threads = os.cpu_count() or 1
+        done_b, t_cpu, k = 0, 0.0, 0
+        while k < n_req and t_cpu < args.cpu_seconds:
+            key, c, pg = I.request(k)
+            col = I.host_column(key, c, pg)
+            t = time.perf_counter()
+            r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets,
+                              threads=threads)
+            t_cpu += time.perf_counter() - t
+            done_b += r.total
+            k += 1
+        extra["cpu_baseline"] = {"value": round(done_b / t_cpu / 1e9, 4), "unit": "GB/s", "cores": threads,
+                                 "kind": "oracle", "sample": f"first {k} requests ({done_b} decoded bytes), "
+                                                             f"{t_cpu:.1f} s"}
+    st2 = srv.stats()
+    srv.destroy()
+    faulthandler.cancel_dump_traceback_later()
+    waves = st1["waves"] - st0["waves"]
+    line = {
+        "metric": SERVE_METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": n_req, "warmup": warm, "ms_per_step": round(float(la.mean()), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "latency_ms": {"p50": round(float(np.percentile(la, 50)), 3), "p99": round(float(np.percentile(la, 99)), 3),
+                       "mean": round(float(la.mean()), 3), "max": round(float(la.max()), 3)},
+        "config": {"workload": args.workload, "description": desc, "arrival_rate": rate, "seconds": seconds,
+                   "requests": n_req, "decoded_bytes": tot_bytes, "offered_gbs": round(tot_bytes / seconds / 1e9, 2),
+                   "late_submissions": late, "n_streams": args.serve_streams, "max_wave": args.serve_wave,
+                   "waves": waves, "mean_wave": round((st1["admitted"] - st0["admitted"]) / max(waves, 1), 2),
+                   "dict_hits": st1["dict_hits"] - st0["dict_hits"],
+                   "dict_misses": st1["dict_misses"] - st0["dict_misses"],
+                   "peak_inflight_bytes": st2["peak_inflight_bytes"], "hbm_budget": budget,
+                   "generation_s": round(t_gen, 1), "parallelism": "single GPU",
+                   "ms_per_step": "mean request latency"},
+        "clocks": clocks,
+        "gpu_launches": 2 * waves,   # per wave: the index pass and the persistent decode kernel
+    }
+    line.update(extra)
+    if "e2e" not in line:
+        line["e2e"] = None
+    print(json.dumps(line), flush=True)
+
+
+def run_served_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    rate, seconds, lo, hi, n_keys, budget, desc = SERVE_WORKLOADS[args.workload]
+    I = ServeInputs(rate, seconds, lo, hi, n_keys, seed=0)
+    threads = os.cpu_count() or 1
+    per_step = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
+    vals, k, last = [], 0, (0, 0, 0.0)
+    for s_i in range(args.warmup + args.steps):
+        done_b, t_cpu, first = 0, 0.0, k
+        while t_cpu < per_step:
+            key, c, pg = I.request(k % I.arrivals.size)
+            col = I.host_column(key, c, pg)
+            t = time.perf_counter()
+            r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets,
+                              threads=threads)
+            t_cpu += time.perf_counter() - t
+            done_b += r.total
+            k += 1
+        if s_i >= args.warmup:
+            vals.append(done_b / t_cpu / 1e9)
+            last = (k - first, done_b, t_cpu)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": SERVE_METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(last[2] * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{last[0]} whole requests ({last[1]} decoded bytes) per step"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="onpair12_10m", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--workload", default="onpair12_10m",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed decoding before warm-up")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -696,12 +1074,24 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the baselines and the e2e leg")
     ap.add_argument("--variant", type=int, default=-1, help="decode variant (-1: built-in default)")
     ap.add_argument("--n-strings", type=int, default=0, help="override the workload's string count")
+    ap.add_argument("--serve-seconds", type=float, default=0.0, help="served: length of the arrival process")
+    ap.add_argument("--serve-streams", type=int, default=4, help="served: concurrent waves")
+    ap.add_argument("--serve-wave", type=int, default=256, help="served: requests per wave")
+    ap.add_argument("--serve-saturation", type=int, default=2000, help="served: requests of the closed-loop run")
+    ap.add_argument("--serve-plain", type=int, default=500, help="served: requests of the per-request baselines")
+    ap.add_argument("--serve-stall", type=float, default=60.0, help="served: give up after this long without a result")
+    ap.add_argument("--serve-watchdog", type=float, default=300.0, help="served: dump thread stacks every N s")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local_rank = env_rank()
     batched = args.workload in BATCH_WORKLOADS
+    served = args.workload in SERVE_WORKLOADS
     if args.impl == "reference":
-        (run_batched_reference if batched else run_reference)(args, rank, world)
+        (run_batched_reference if batched else run_served_reference if served else run_reference)(args, rank, world)
+    elif served:
+        if world > 1 and rank != 0:
+            return   # one server per GPU is the product's unit; the served bench runs on rank 0
+        run_served(args, rank, world, local_rank)
     elif batched:
         run_batched(args, rank, world, local_rank)
     else:

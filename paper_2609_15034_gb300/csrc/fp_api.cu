@@ -73,12 +73,13 @@ fp_status get_workspace(cudaStream_t stream, size_t tiles, size_t plain_words, W
         const size_t bytes = kWsHeaderBytes + cap * sizeof(unsigned long long) + (cap + 1) * sizeof(uint32_t);
         e = cudaMalloc(&w->d_mem, bytes);
         if (e != cudaSuccess) { w->d_mem = nullptr; return cuda_fail(e, "cudaMalloc(workspace)"); }
-        e = cudaMemset(w->d_mem, 0, bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(workspace)");
-        unsigned one = 1;   // epoch 0 is reserved for "never written"
-        e = cudaMemcpy(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, epoch), &one, sizeof(one),
-                       cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(epoch)");
+        // initialise in `stream` order, ahead of the launches that use it
+        static const unsigned one = 1;   // epoch 0 is reserved for "never written"
+        e = cudaMemsetAsync(w->d_mem, 0, bytes, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
+        e = cudaMemcpyAsync(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, epoch), &one, sizeof(one),
+                            cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(epoch)");
         w->tiles_cap = cap;
         w->launches = 0;
     }
@@ -188,14 +189,17 @@ fp_status status_code(uint32_t bits) {
 
 namespace {
 
-// Read and clear the workspace status (stream already synchronised).
-fp_status take_status(Workspace* w, uint64_t* total) {
+// Read and clear the workspace status (stream already synchronised); the
+// clear is ordered before the stream's next launch.
+fp_status take_status(Workspace* w, uint64_t* total, cudaStream_t stream) {
     WsHeader h;
     cudaError_t e = cudaMemcpy(&h, w->d_mem, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
     if (h.status) {
-        e = cudaMemset(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, status), 0, sizeof(unsigned));
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        e = cudaMemsetAsync(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, status), 0, sizeof(unsigned),
+                            stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     }
     if (total) *total = h.total;
     return status_from_bits(h.status);
@@ -353,7 +357,7 @@ fp_status fp_decoded_size(fp_codec codec, const fp_dict* dict, const void* d_cod
     if (st != FP_OK) return st;
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    return take_status(w, h_total);
+    return take_status(w, h_total, stream);
 }
 
 fp_status fp_decode_plain(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
@@ -391,7 +395,7 @@ fp_status fp_sync_status(fp_stream_t stream_) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     Workspace* w = find_workspace(stream);
     if (!w || !w->d_mem) return FP_OK;
-    return take_status(w, nullptr);
+    return take_status(w, nullptr, stream);
 }
 
 int fp_variant_count(fp_codec codec) { return valid_codec(codec) ? variant_count(codec) : 0; }
@@ -458,6 +462,8 @@ fp_status noalloc_setup(NoAllocDevice** out) {
         const unsigned one = 1;   // launch tag 0 means "never written"
         e = cudaMemcpy(static_cast<char*>(ptr) + offsetof(WsHeader, epoch), &one, sizeof(one),
                        cudaMemcpyHostToDevice);
+        // complete before any stream (blocking or not) launches on the array
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(scratch epoch)");
         d.ptr = ptr;
         d.ready = true;

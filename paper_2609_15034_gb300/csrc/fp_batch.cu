@@ -336,6 +336,8 @@ fp_status build_layout(fp_plan* P, int cfg) {
     relocate(L, base);
     e = cudaMemcpy(base, L.bytes.data(), L.table_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(base + L.table_bytes, 0, L.total_bytes - L.table_bytes);
+    // the legacy-stream memset must be complete before launches on any stream
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "batch layout upload");
     uint32_t split[2];
     int grid = 0;
@@ -512,6 +514,12 @@ fp_status plan_create(const fp_chunk* chunks, uint32_t n, int force_cfg, const c
         if (cap) cudaStreamDestroy(cap);
         if (e != cudaSuccess) st = cuda_fail(e, "batch graph capture");
     }
+    // every initialisation above ran on the legacy stream or the tuning
+    // stream: complete it before the plan is launched on any stream
+    if (st == FP_OK) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "plan creation");
+    }
     if (st != FP_OK) {
         const std::string msg = fp_last_error();
         plan_release(P);
@@ -544,6 +552,7 @@ fp_status wave_init(WaveBuffers& W, uint32_t cap_chunks) {
     if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&W.h_status), cap_chunks * sizeof(uint32_t) + 64, 0);
     if (e == cudaSuccess)
         e = cudaHostAlloc(reinterpret_cast<void**>(&W.h_total), cap_chunks * sizeof(unsigned long long), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // initialised before any lane stream uses it
     if (e != cudaSuccess) {
         wave_free(W);
         return cuda_fail(e, "wave buffers");
@@ -581,7 +590,7 @@ fp_status wave_launch(WaveBuffers& W, const fp_chunk* chunks, uint32_t n, int co
         size_t cap = 1u << 20;
         while (cap < L.total_bytes) cap *= 2;
         if (e == cudaSuccess) e = cudaMalloc(&W.d_layout, cap);
-        if (e == cudaSuccess) e = cudaMemset(W.d_layout, 0, cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(W.d_layout, 0, cap, stream);   // ordered before the upload
         if (e != cudaSuccess) { W.d_layout = nullptr; return cuda_fail(e, "wave layout"); }
         W.layout_cap = cap;
     }
@@ -676,9 +685,12 @@ fp_status fp_plan_sync_status(fp_plan* plan, fp_stream_t stream_, uint32_t* h_ch
     if (e == cudaSuccess) e = cudaMemcpy(bits.data(), plan->d_status, n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && h_chunk_total)
         e = cudaMemcpy(h_chunk_total, plan->d_total, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, n * sizeof(uint32_t));
+    // clears ordered before the stream's next launch
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_status, 0, n * sizeof(uint32_t), stream);
     if (e == cudaSuccess && h.status)
-        e = cudaMemset(static_cast<char*>(plan->d_hdr) + offsetof(WsHeader, status), 0, sizeof(unsigned));
+        e = cudaMemsetAsync(static_cast<char*>(plan->d_hdr) + offsetof(WsHeader, status), 0, sizeof(unsigned),
+                            stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "plan status");
     uint32_t all = h.status;
     uint32_t first_bad = n;

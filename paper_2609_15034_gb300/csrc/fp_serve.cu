@@ -243,12 +243,22 @@ void lane_launch(fp_server* S, Lane& L) {
                 e = cudaStreamWaitEvent(L.s, sl.ready, 0);
             }
             if (e != cudaSuccess) {
-                // leave the slot empty and the request queued; report through the stats' error text
+                // the device refused the dictionary's upload: fail this request (a dead context
+                // fails every later one the same way instead of leaving them queued)
                 S->sched_error = cudaGetErrorString(e);
                 S->dicts.at(q->r.dict_key).slot = -1;
                 sl.used = false;
                 S->arena.release(off, need);
-                break;
+                S->pending.pop_front();
+                q->status = (uint32_t)FP_ERR_CUDA;
+                q->t_admit = q->t_done = now_ns();
+                q->done = true;
+                q->block = 0;
+                S->st.completed++;
+                S->st.failed++;
+                S->finished.push_back(q);
+                S->cv_done.notify_all();
+                continue;
             }
             sl.refs++;
             sl.lru = ++S->lru_clock;

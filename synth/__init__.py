@@ -468,3 +468,30 @@ def pool_window(pool: Column, start: int, n_strings: int):
     slot0 = byte0 * 8 // w
     end_byte = (int(co[-1]) * w + 7) // 8
     return byte0, end_byte, (co - slot0).astype(np.uint32)
+
+
+def same_shape_dictionary(base: Dictionary, seed: int) -> Dictionary:
+    """A distinct dictionary with the token lengths of `base` code by code:
+    the tokens of each length are permuted among the codes of that length
+    (seeded).  Every code stream then decodes to the same number of bytes
+    under `base` and under the new dictionary."""
+    rng = rng_for(5, seed, base.codec)
+    lens = base.token_lengths()
+    idx = np.arange(lens.size)
+    for L in np.unique(lens):
+        sel = np.nonzero(lens == L)[0]
+        idx[sel] = sel[rng.permutation(sel.size)]
+    offs = base.offsets.astype(np.int64)
+    src = np.repeat(offs[:-1][idx] - offs[:-1], lens) + np.arange(int(offs[-1]))
+    return Dictionary(base.codec, base.data[src].copy(), base.offsets.copy())
+
+
+def slot_bytes(col: Column) -> np.ndarray:
+    """Decoded bytes each slot of a generated column contributes (from the
+    generator's bookkeeping and the token lengths): the column's length
+    profile, for sizing outputs of windows of it."""
+    lens = col.dictionary.token_lengths()
+    if col.codec == FSST8:
+        codes = np.minimum(col.slot_codes, lens.size - 1)
+        return np.where(col.slot_is_literal, 1, np.where(col.slot_codes == FSST_ESCAPE, 0, lens[codes]))
+    return lens[col.slot_codes]
