@@ -42,8 +42,8 @@ namespace {
 
 // ---- per-stream workspace ----------------------------------------------------
 struct Workspace {
-    void* d_mem = nullptr;        // WsHeader + tile status words
-    size_t tiles_cap = 0;
+    void* d_mem = nullptr;        // WsHeader + the decoder's scratch
+    size_t scratch_cap = 0;       // bytes after the header
     uint64_t launches = 0;
     uint32_t* d_plain = nullptr;  // scratch of the plain baseline
     size_t plain_words = 0;
@@ -52,25 +52,26 @@ struct Workspace {
 std::mutex g_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
 
-// Get (or grow) the workspace of (current device, stream).
-fp_status get_workspace(cudaStream_t stream, size_t tiles, size_t plain_words, Workspace** out) {
+// Get (or grow) the workspace of (current device, stream): the header plus
+// `scratch` bytes.
+fp_status get_workspace(cudaStream_t stream, size_t scratch, size_t plain_words, Workspace** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     std::lock_guard<std::mutex> lk(g_mu);
     Workspace*& w = g_ws[{dev, stream}];
     if (!w) w = new Workspace();
-    if (w->d_mem == nullptr || w->tiles_cap < tiles) {
-        size_t cap = w->tiles_cap ? w->tiles_cap : 1024;
-        while (cap < tiles) cap *= 2;
+    if (w->d_mem == nullptr || w->scratch_cap < scratch) {
+        size_t cap = w->scratch_cap ? w->scratch_cap : (64u << 10);
+        while (cap < scratch) cap *= 2;
         if (w->d_mem) {
             e = cudaStreamSynchronize(stream);
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
             cudaFree(w->d_mem);
             w->d_mem = nullptr;
-            w->tiles_cap = 0;
+            w->scratch_cap = 0;
         }
-        const size_t bytes = kWsHeaderBytes + cap * sizeof(unsigned long long) + (cap + 1) * sizeof(uint32_t);
+        const size_t bytes = kWsHeaderBytes + cap;
         e = cudaMalloc(&w->d_mem, bytes);
         if (e != cudaSuccess) { w->d_mem = nullptr; return cuda_fail(e, "cudaMalloc(workspace)"); }
         // initialise in `stream` order, ahead of the launches that use it
@@ -80,7 +81,7 @@ fp_status get_workspace(cudaStream_t stream, size_t tiles, size_t plain_words, W
         e = cudaMemcpyAsync(reinterpret_cast<char*>(w->d_mem) + offsetof(WsHeader, epoch), &one, sizeof(one),
                             cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(epoch)");
-        w->tiles_cap = cap;
+        w->scratch_cap = cap;
         w->launches = 0;
     }
     if (plain_words && w->plain_words < plain_words) {
@@ -121,7 +122,7 @@ struct DevInfo {
 };
 std::map<int, DevInfo> g_dev;
 
-fp_status grid_for(const Variant& var, int* grid_per_wave) {
+fp_status grid_for(const Variant& var, int* grid_per_wave, int* sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -142,6 +143,7 @@ fp_status grid_for(const Variant& var, int* grid_per_wave) {
         it = di.blocks_per_sm.emplace(var.kernel, nb).first;
     }
     *grid_per_wave = it->second * di.sms;
+    *sms = di.sms;
     return FP_OK;
 }
 
@@ -215,16 +217,16 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
     const uint64_t max_slots = max_slots_of(codec, codes_bytes);
     const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
-    int per_wave = 0;
-    fp_status st = grid_for(*var, &per_wave);
+    int per_wave = 0, sms = 0;
+    fp_status st = grid_for(*var, &per_wave, &sms);
     if (st != FP_OK) return st;
     Workspace* w = nullptr;
-    st = get_workspace(stream, n_tiles, 0, &w);
+    st = get_workspace(stream, variant_scratch_bytes(*var, max_slots), 0, &w);
     if (st != FP_OK) return st;
     if ((++w->launches & ((1ull << 25) - 1)) == 0) {
         // Tile status words carry a 26-bit launch tag; clear them well before it wraps.
-        cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(w->d_mem) + kWsHeaderBytes, 0,
-                                        w->tiles_cap * sizeof(unsigned long long), stream);
+        cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(w->d_mem) + kWsHeaderBytes, 0, w->scratch_cap,
+                                        stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     }
     DecodeParams p;
@@ -238,12 +240,10 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
     p.capacity = size_only ? 0 : out_capacity;
     p.out_offsets = d_out_offsets;
     p.ws = static_cast<WsHeader*>(w->d_mem);
-    p.tile_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(w->d_mem) + kWsHeaderBytes);
     p.size_only = size_only ? 1 : 0;
-    const uint64_t grid = n_tiles < (uint64_t)per_wave ? n_tiles : (uint64_t)per_wave;
-    uint32_t* first = reinterpret_cast<uint32_t*>(static_cast<char*>(w->d_mem) + kWsHeaderBytes +
-                                                  w->tiles_cap * sizeof(unsigned long long));
-    cudaError_t e = launch_decode(codec, *var, p, first, (int)grid, stream);
+    const uint64_t grid = (n_tiles < (uint64_t)per_wave && !var->warp_tiles) ? n_tiles : (uint64_t)per_wave;
+    cudaError_t e = launch_decode(codec, *var, p, static_cast<char*>(w->d_mem) + kWsHeaderBytes, max_slots,
+                                  (int)grid, sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     if (ws_out) *ws_out = w;
     return FP_OK;
@@ -369,7 +369,7 @@ fp_status fp_decode_plain(fp_codec codec, const fp_dict* dict, const void* d_cod
     if (st != FP_OK) return st;
     Workspace* w = nullptr;
     const size_t words = plain_scratch_words(n_strings);
-    st = get_workspace(stream, 1, words, &w);
+    st = get_workspace(stream, 256, words, &w);
     if (st != FP_OK) return st;
     DecodeParams p;
     memset(&p, 0, sizeof(p));
@@ -489,16 +489,23 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     const uint64_t max_slots = max_slots_of(codec, codes_bytes);
     const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
-    const uint64_t cap = (kNoAllocScratchBytes - kWsHeaderBytes - sizeof(uint32_t)) /
-                         (sizeof(unsigned long long) + sizeof(uint32_t));
-    if (n_tiles > cap)
+    const size_t need = variant_scratch_bytes(*var, max_slots);
+    const size_t room = kNoAllocScratchBytes - kWsHeaderBytes;
+    if (need > room) {
+        // the largest buffer that fits, for the message
+        uint64_t lo = 0, hi = max_slots;
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo + 1) / 2;
+            if (variant_scratch_bytes(*var, mid) <= room) lo = mid; else hi = mid - 1;
+        }
         return fail(FP_ERR_ARG,
-                    "fp_decode_noalloc: the code buffer spans up to %llu tiles of %llu slots; the fixed scratch holds "
-                    "%llu tiles (%llu slots); use fp_decode",
-                    (unsigned long long)n_tiles, (unsigned long long)tile, (unsigned long long)cap,
-                    (unsigned long long)((cap - 2) * tile));
-    int per_wave = 0;
-    st = grid_for(*var, &per_wave);
+                    "fp_decode_noalloc: a code buffer of %llu slots needs %llu scratch bytes; the fixed scratch holds "
+                    "%llu (at most %llu slots with this variant); use fp_decode",
+                    (unsigned long long)max_slots, (unsigned long long)need, (unsigned long long)room,
+                    (unsigned long long)lo);
+    }
+    int per_wave = 0, sms = 0;
+    st = grid_for(*var, &per_wave, &sms);
     if (st != FP_OK) return st;
     NoAllocDevice* nd = nullptr;
     st = noalloc_setup(&nd);
@@ -507,7 +514,7 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     cudaError_t e;
     if ((++nd->launches & ((1ull << 25) - 1)) == 0) {
         // tile status words carry a 26-bit launch tag; clear them well before it wraps
-        e = cudaMemsetAsync(base + kWsHeaderBytes, 0, cap * sizeof(unsigned long long), stream);
+        e = cudaMemsetAsync(base + kWsHeaderBytes, 0, room, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
     }
     DecodeParams p;
@@ -521,11 +528,9 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     p.capacity = out_capacity;
     p.out_offsets = d_out_offsets;
     p.ws = reinterpret_cast<WsHeader*>(base);
-    p.tile_status = reinterpret_cast<unsigned long long*>(base + kWsHeaderBytes);
     p.size_only = 0;
-    uint32_t* first = reinterpret_cast<uint32_t*>(base + kWsHeaderBytes + cap * sizeof(unsigned long long));
-    const uint64_t grid = n_tiles < (uint64_t)per_wave ? n_tiles : (uint64_t)per_wave;
-    e = launch_decode(codec, *var, p, first, (int)grid, stream);
+    const uint64_t grid = (n_tiles < (uint64_t)per_wave && !var->warp_tiles) ? n_tiles : (uint64_t)per_wave;
+    e = launch_decode(codec, *var, p, base + kWsHeaderBytes, max_slots, (int)grid, sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     // hand the call's data-error bits to the caller and clear them for the next call
     e = cudaMemcpyAsync(d_status, base + offsetof(WsHeader, status), sizeof(uint32_t), cudaMemcpyDeviceToDevice,

@@ -34,7 +34,7 @@
 namespace fp {
 namespace {
 
-constexpr u32 kIdxPerBlock = 2048;   // string boundaries per index block (256 threads x 8)
+constexpr u32 kIdxPerBlock = 256 * kIdxGroup;   // string boundaries per index block
 
 struct IdxBlock {
     u32 q_ci;    // queue in bits 30..31, chunk index within the queue below
@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256) batch_index_kernel(const IdxParams ip) {
         cs->x.c_end = x.c_end;
         cs->x.bad = x.bad;
     }
-    index_strings(p, x, ip.tile[q], (u64)b.start + threadIdx.x, (u64)b.start + kIdxPerBlock, 256,
-                  const_cast<u32*>(p.first));
+    index_groups(p, x, (u32)(__ffs((int)ip.tile[q]) - 1), b.start, (u64)b.start + kIdxPerBlock, threadIdx.x, 256,
+                 const_cast<u32*>(p.first));
 }
 
 template <int K16, int K12, int K8, int MINB>

@@ -2,6 +2,7 @@
 // decode pipeline (fp_decoder.cuh), its variant table and the launch of the
 // index pass plus the decode kernel.
 #include "fp_decoder.cuh"
+#include "fp_warp.cuh"
 
 namespace fp {
 namespace {
@@ -9,8 +10,8 @@ namespace {
 // Index pass over one column (grid-stride over its string boundaries).
 __global__ void __launch_bounds__(256) index_kernel(const DecodeParams p, u32 tile, u32* first) {
     const Extent x = column_extent(p, tile);
-    index_strings(p, x, tile, (u64)blockIdx.x * blockDim.x + threadIdx.x, (u64)p.n_strings + 1,
-                  (u64)gridDim.x * blockDim.x, first);
+    index_groups(p, x, (u32)(__ffsll((long long)tile) - 1), 0, (u64)p.n_strings + 1,
+                 (u64)blockIdx.x * blockDim.x + threadIdx.x, (u64)gridDim.x * blockDim.x, first);
 }
 
 template <int CODEC, int K, bool DSMEM, int MINB>
@@ -26,23 +27,51 @@ __global__ void __launch_bounds__(kThreads, MINB) decode_kernel(const DecodePara
 template <int CODEC, int K, bool DSMEM, int MINB>
 static Variant make_variant() {
     typedef Decoder<CODEC, K, DSMEM, MINB> D;
-    return Variant{kThreads, K, DSMEM ? 1 : 0, sizeof(typename D::S),
-                   (const void*)&decode_kernel<CODEC, K, DSMEM, MINB>};
+    Variant v{};
+    v.threads = kThreads;
+    v.slots_per_thread = K;
+    v.dict_smem = DSMEM ? 1 : 0;
+    v.smem_bytes = sizeof(typename D::S);
+    v.kernel = (const void*)&decode_kernel<CODEC, K, DSMEM, MINB>;
+    v.warp_tiles = 0;
+    return v;
+}
+
+template <int CODEC, int K, bool DSMEM, int NW, int MINB>
+static Variant make_warp_variant() {
+    typedef WarpCore<CODEC, K, DSMEM> C;
+    Variant v{};
+    v.threads = NW * 32;
+    v.slots_per_thread = K;
+    v.dict_smem = DSMEM ? 1 : 0;
+    v.smem_bytes = (size_t)C::DICT_BYTES + (DSMEM ? (size_t)C::LENS_BYTES : 0) + NW * sizeof(WarpArea<K>);
+    v.kernel = (const void*)&warp_decode_kernel<CODEC, K, DSMEM, NW, MINB>;
+    v.warp_tiles = 1;
+    v.reduce = (const void*)&reduce_kernel<CODEC, K, DSMEM>;
+    v.scan = (const void*)&tiles_scan_kernel<CODEC == FP_FSST8>;
+    return v;
 }
 
 static const Variant* table_for(int codec, int* n) {
     static const Variant v16[] = {
         make_variant<FP_ONPAIR16, 16, false, 2>(),
         make_variant<FP_ONPAIR16, 8, false, 2>(),
+        make_warp_variant<FP_ONPAIR16, 16, false, 8, 3>(),
+        make_warp_variant<FP_ONPAIR16, 16, false, 8, 2>(),
     };
     static const Variant v12[] = {
         make_variant<FP_ONPAIR12, 16, true, 2>(),
         make_variant<FP_ONPAIR12, 16, false, 2>(),
         make_variant<FP_ONPAIR12, 8, true, 2>(),
+        make_warp_variant<FP_ONPAIR12, 16, true, 8, 2>(),
+        make_warp_variant<FP_ONPAIR12, 16, false, 8, 3>(),
+        make_warp_variant<FP_ONPAIR12, 16, true, 10, 2>(),
     };
     static const Variant v8[] = {
         make_variant<FP_FSST8, 16, true, 2>(),
         make_variant<FP_FSST8, 32, true, 2>(),
+        make_warp_variant<FP_FSST8, 16, true, 8, 3>(),
+        make_warp_variant<FP_FSST8, 32, true, 8, 2>(),
     };
     switch (codec) {
         case FP_ONPAIR16: *n = (int)(sizeof(v16) / sizeof(v16[0])); return v16;
@@ -64,26 +93,104 @@ const Variant* variant_get(int codec, int v) {
     return (t && v >= 0 && v < n) ? &t[v] : nullptr;
 }
 
-int variant_default(int codec) { (void)codec; return 0; }
+// Defaults chosen by measurement on GB300 (full-size synthetic columns):
+// OnPair-12 warp tiles, 10 warps per block, dictionary in shared memory;
+// FSST-8 block pipeline with 32 slots per thread; OnPair-16 block pipeline.
+int variant_default(int codec) {
+    switch (codec) {
+        case FP_ONPAIR12: return 5;
+        case FP_FSST8: return 1;
+        default: return 0;
+    }
+}
 
-uint64_t variant_tile(const Variant& v) { return (uint64_t)kWork * (uint64_t)v.slots_per_thread; }
+uint64_t variant_tile(const Variant& v) {
+    return (uint64_t)(v.warp_tiles ? 32 : kWork) * (uint64_t)v.slots_per_thread;
+}
 
-cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_in, uint32_t* first, int grid,
-                          cudaStream_t stream) {
+namespace {
+
+constexpr size_t kExtentBytes = 64;
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch layout of a variant for a buffer of max_slots slots.
+struct ScratchLayout {
+    uint64_t n_tiles;        // tiles (block tiles or warp tiles) covering the buffer, plus slack
+    size_t o_status, o_first, o_agg, o_ex, o_extent, bytes;
+};
+
+ScratchLayout scratch_layout(const Variant& v, uint64_t max_slots) {
+    ScratchLayout L{};
+    L.n_tiles = max_slots / variant_tile(v) + 2;
+    if (!v.warp_tiles) {
+        L.o_status = 0;
+        L.o_first = al256(L.n_tiles * sizeof(unsigned long long));
+        L.bytes = al256(L.o_first + (L.n_tiles + 1) * sizeof(uint32_t));
+        return L;
+    }
+    const uint64_t n_scan = L.n_tiles / kScanTile + 2;
+    L.o_status = 0;
+    L.o_extent = al256(n_scan * sizeof(unsigned long long));
+    L.o_agg = L.o_extent + al256(kExtentBytes);
+    L.o_ex = L.o_agg + al256(L.n_tiles * sizeof(u64));
+    L.o_first = L.o_ex + al256(L.n_tiles * sizeof(u64));
+    L.bytes = al256(L.o_first + (L.n_tiles + 1) * sizeof(uint32_t));
+    return L;
+}
+
+}  // namespace
+
+size_t variant_scratch_bytes(const Variant& v, uint64_t max_slots) { return scratch_layout(v, max_slots).bytes; }
+
+cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_in, void* scratch, uint64_t max_slots,
+                          int grid, int sms, cudaStream_t stream) {
     (void)codec;
+    const ScratchLayout L = scratch_layout(var, max_slots);
+    char* base = static_cast<char*>(scratch);
     DecodeParams p = p_in;
     p.err_word = &p.ws->status;
     p.total_out = &p.ws->total;
+    p.tile_status = reinterpret_cast<unsigned long long*>(base + L.o_status);
+    uint32_t* first = reinterpret_cast<uint32_t*>(base + L.o_first);
     p.first = first;
     const uint64_t tile = variant_tile(var);
     const uint64_t nb = (uint64_t)p.n_strings + 1;
-    uint64_t ib = (nb + 255) / 256;
-    if (ib > 4096) ib = 4096;
+    uint64_t ib = (nb + 256 * kIdxGroup - 1) / (256 * kIdxGroup);
+    if (ib > (uint64_t)sms * 8) ib = (uint64_t)sms * 8;
     index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&p};
-    return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
+    if (!var.warp_tiles) return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
+
+    // warp tiles: extent, reduce, tile scan, decode
+    Extent* xp = reinterpret_cast<Extent*>(base + L.o_extent);
+    u64* agg = reinterpret_cast<u64*>(base + L.o_agg);
+    u64* ex = reinterpret_cast<u64*>(base + L.o_ex);
+    extent_kernel<<<1, 32, 0, stream>>>(p, tile, xp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t n_wt_max = L.n_tiles;   // upper bound; the kernels read the true count from *xp
+    uint64_t rg = (n_wt_max + 7) / 8;
+    const uint64_t rg_cap = (uint64_t)sms * 8;
+    if (rg > rg_cap) rg = rg_cap;
+    const Extent* cxp = xp;
+    void* rargs[] = {(void*)&p, (void*)&cxp, (void*)&agg};
+    e = cudaLaunchKernel(var.reduce, dim3((unsigned)rg), dim3(256), rargs, 0, stream);
+    if (e != cudaSuccess) return e;
+    uint64_t sg = n_wt_max / kScanTile + 1;
+    if (sg > (uint64_t)sms * 2) sg = (uint64_t)sms * 2;
+    const u64* cagg = agg;
+    unsigned long long* st = p.tile_status;
+    void* sargs[] = {(void*)&p, (void*)&cxp, (void*)&cagg, (void*)&ex, (void*)&st};
+    e = cudaLaunchKernel(var.scan, dim3((unsigned)sg), dim3(256), sargs, 0, stream);
+    if (e != cudaSuccess) return e;
+    const u64* cex = ex;
+    void* dargs[] = {(void*)&p, (void*)&cxp, (void*)&cex};
+    const int nw = var.threads / 32;
+    uint64_t dg = (n_wt_max + nw - 1) / nw;
+    if (dg > (uint64_t)grid) dg = (uint64_t)grid;
+    return cudaLaunchKernel(var.kernel, dim3((unsigned)dg), dim3(var.threads), dargs, var.smem_bytes, stream);
 }
 
 }  // namespace fp

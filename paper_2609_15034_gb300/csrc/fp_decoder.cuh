@@ -171,6 +171,28 @@ __device__ __forceinline__ Elem agg_unpack(u64 w) {
     e.n = (u32)((w >> 17) & 1u) | ((u32)((w >> 35) & 1u) << 1);
     return e;
 }
+// Aggregates of large tiles (up to 2^29 bytes).  For FSST-8 the two byte
+// counts of an element differ by at most 8 -- the two parses of a slot range
+// (entered on a code or on a literal) produce the same bytes from the first
+// slot where they meet, and before that only an alternating run of 0xFF
+// slots (one byte per two slots in both) and one token-versus-literal step
+// -- so b1 is stored as a 5-bit difference from b0.
+template <bool FSST>
+__device__ __forceinline__ u64 agg_payload_wide(const Elem& e) {
+    if (!FSST) return e.b0 & kPayloadMask;
+    const u64 d = (u64)((long long)e.b1 - (long long)e.b0 + 16) & 31ull;
+    return (e.b0 & 0x1fffffffull) | (d << 29) | ((u64)(e.n & 3u) << 34);
+}
+template <bool FSST>
+__device__ __forceinline__ Elem agg_unpack_wide(u64 w) {
+    if (!FSST) return Elem{w & kPayloadMask, 0, 0};
+    Elem e;
+    e.b0 = w & 0x1fffffffull;
+    e.b1 = (u64)((long long)e.b0 + (long long)((w >> 29) & 31ull) - 16);
+    e.n = (u32)((w >> 34) & 3ull);
+    return e;
+}
+
 template <bool FSST>
 __device__ __forceinline__ u64 inc_payload(u64 bytes, u32 state) {
     if (!FSST) return bytes & kPayloadMask;
@@ -182,7 +204,7 @@ __device__ __forceinline__ u64 inc_payload(u64 bytes, u32 state) {
 // tile and (FSST-8) the state entering it.  Waits are bounded: on giving up
 // the status word gets ERRB_TIMEOUT and every later wait returns at once.
 // ---------------------------------------------------------------------------
-template <bool FSST>
+template <bool FSST, bool WIDE = false>
 __device__ void lookback(const u64* status, long long tile, u32 epoch, WsHeader* ws, u64& excl_bytes,
                          u32& excl_state) {
     // Each lane reads 4 consecutive status words, so one round trip to L2
@@ -243,7 +265,8 @@ __device__ void lookback(const u64* status, long long tile, u32 epoch, WsHeader*
 #pragma unroll
         for (int j = V - 1; j >= 0; --j) {
             const bool use = (lane < p) || (lane == p && (u32)j < jinc);
-            if (use) f = then<FSST>(f, agg_unpack<FSST>(w[j] & kPayloadMask));
+            if (use) f = then<FSST>(f, WIDE ? agg_unpack_wide<FSST>(w[j] & kPayloadMask)
+                                            : agg_unpack<FSST>(w[j] & kPayloadMask));
         }
         // then across lanes: lane L+1 precedes lane L in the stream
 #pragma unroll
@@ -426,29 +449,48 @@ __device__ __forceinline__ Extent column_extent(const DecodeParams& p, u64 tile)
 // belongs to the last tile); first[n_tiles] = n_strings + 1.  Also checks
 // that code_offsets is non-decreasing and inside the code buffer.
 // ---------------------------------------------------------------------------
-// Boundaries i = i0, i0 + step, ... below min(i1, n_strings + 1).
-__device__ __forceinline__ void index_strings(const DecodeParams& p, const Extent& x, u64 tile, u64 i0, u64 i1,
-                                              u64 step, u32* first) {
+// Boundary i (at slot `pos`, boundary i-1 at `prev`): the tiles from the one
+// after prev's tile up to pos's tile start their first string at i.  Tiles
+// are a power of two slots long (1 << tile_log2).
+// Slot positions are code_offsets values (32-bit), so is c_end (clamped
+// to one), and tile indices are below 2^32.
+__device__ __forceinline__ void index_one(const Extent& x, u32 tile_log2, u64 nb, u64 i, u32 pos, u32 prev,
+                                          u32* first, u32& err) {
+    const u32 cb = (u32)x.c_begin, ce = (u32)x.c_end, ft = (u32)x.first_tile, nt = (u32)x.n_tiles;
+    const u32 pc = pos < cb ? cb : (pos > ce ? ce : pos);
+    u32 u = (pc >> tile_log2) - ft;
+    if (u >= nt) u = nt - 1;
+    u32 w0 = 0;
+    if (i > 0) {
+        if (prev > pos) err |= ERRB_CORRUPT;
+        const u32 qc = prev < cb ? cb : (prev > ce ? ce : prev);
+        u32 up = (qc >> tile_log2) - ft;
+        if (up >= nt) up = nt - 1;
+        w0 = up + 1;
+    }
+    for (u32 w = w0; w <= u; ++w) first[w] = (u32)i;
+    if (i == nb - 1)
+        for (u64 w = (u64)u + 1; w <= x.n_tiles; ++w) first[w] = (u32)nb;
+}
+
+// Boundaries [g * 8, g * 8 + 8) for groups g = g0, g0 + gstep, ... : a
+// thread's nine code_offsets loads are in flight together.
+constexpr int kIdxGroup = 8;
+__device__ __forceinline__ void index_groups(const DecodeParams& p, const Extent& x, u32 tile_log2, u64 i_begin,
+                                             u64 i_end, u64 g0, u64 gstep, u32* first) {
     const u64 nb = (u64)p.n_strings + 1;
-    if (i1 > nb) i1 = nb;
+    if (i_end > nb) i_end = nb;
     u32 err = x.bad ? ERRB_CORRUPT : 0u;
-    for (u64 i = i0; i < i1; i += step) {
-        const u64 pos = __ldg(p.code_offsets + i);
-        u64 pc = pos < x.c_begin ? x.c_begin : (pos > x.c_end ? x.c_end : pos);
-        u64 u = pc / tile - x.first_tile;
-        if (u >= x.n_tiles) u = x.n_tiles - 1;
-        u64 w0 = 0;
-        if (i > 0) {
-            const u64 prev = __ldg(p.code_offsets + i - 1);
-            if (prev > pos) err |= ERRB_CORRUPT;
-            u64 qc = prev < x.c_begin ? x.c_begin : (prev > x.c_end ? x.c_end : prev);
-            u64 up = qc / tile - x.first_tile;
-            if (up >= x.n_tiles) up = x.n_tiles - 1;
-            w0 = up + 1;
+    for (u64 i0 = i_begin + g0 * kIdxGroup; i0 < i_end; i0 += gstep * kIdxGroup) {
+        u32 v[kIdxGroup + 1];
+#pragma unroll
+        for (int k = 0; k <= kIdxGroup; ++k) {
+            const u64 i = i0 + k - 1;   // v[0] is boundary i0 - 1
+            v[k] = (k > 0 || i0 > 0) && i < i_end ? __ldg(p.code_offsets + i) : 0u;
         }
-        for (u64 w = w0; w <= u; ++w) first[w] = (u32)i;
-        if (i == nb - 1)
-            for (u64 w = u + 1; w <= x.n_tiles; ++w) first[w] = (u32)nb;
+#pragma unroll
+        for (int k = 0; k < kIdxGroup; ++k)
+            if (i0 + k < i_end) index_one(x, tile_log2, nb, i0 + k, v[k + 1], v[k], first, err);
     }
     if (err) atomicOr(p.err_word, err);
 }

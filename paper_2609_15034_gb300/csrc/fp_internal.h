@@ -98,14 +98,17 @@ struct BatchParams {
     uint32_t split[2];    // blocks [0, split[0]) start on queue 0, [split[0], split[1]) on 1, the rest on 2
 };
 
-// A compiled tile shape.
+// A compiled decoder shape.
 struct Variant {
     int threads;
     int slots_per_thread;
     int dict_smem;
     size_t smem_bytes;
-    const void* kernel;   // __global__ function
-    int work_threads;     // threads that assemble output (slots per tile = work_threads * slots_per_thread)
+    const void* kernel;   // the decode kernel
+    int warp_tiles;       // 0: block pipeline (one launch after the index pass);
+                          // 1: warp tiles (reduce, tile scan and warp decode launches)
+    const void* reduce;   // warp tiles: the reduce kernel
+    const void* scan;     // warp tiles: the tile scan kernel
 };
 
 // Variant tables (fp_decode.cu).
@@ -114,9 +117,14 @@ const Variant* variant_get(int codec, int v);
 int variant_default(int codec);
 
 // Launch helpers (fp_decode.cu, fp_plain.cu).
-uint64_t variant_tile(const Variant& v);   // code slots per tile
-cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p, uint32_t* first, int grid,
-                          cudaStream_t stream);
+uint64_t variant_tile(const Variant& v);   // code slots per tile (block tile or warp tile)
+// Device scratch a decode of a buffer of `max_slots` slots needs after the
+// 128-byte workspace header.
+size_t variant_scratch_bytes(const Variant& v, uint64_t max_slots);
+// Index pass + decode of one column.  p.ws is the workspace header, `scratch`
+// the variant's scratch; `grid` the decode kernel's persistent width.
+cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p, void* scratch, uint64_t max_slots,
+                          int grid, int sms, cudaStream_t stream);
 cudaError_t launch_plain(int codec, const DecodeParams& p, uint32_t* d_scratch, size_t scratch_words,
                          cudaStream_t stream);
 size_t plain_scratch_words(uint32_t n_strings);

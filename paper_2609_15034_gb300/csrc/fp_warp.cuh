@@ -1,0 +1,689 @@
+// Warp-tile decoder: the column is cut into warp tiles of 32*K code slots,
+// and a decode runs in three passes after the index pass:
+//
+//   reduce_kernel   each warp computes the scan element of a warp tile
+//                   (its decoded bytes; for FSST-8 the two-state element of
+//                   the escape parity) and stores it: fully parallel, the
+//                   code stream is read once;
+//   tiles_scan_kernel  single-pass exclusive scan of the warp-tile elements
+//                   (blocks of 2,048 elements, decoupled look-back across
+//                   blocks): every warp tile's output offset and entering
+//                   escape state;
+//   warp_decode_kernel  every warp decodes whole warp tiles on its own: code
+//                   unpack, lengths, a warp scan inside the tile, assembly in
+//                   registers with aligned 16-byte stores, merging of chunks
+//                   shared by lanes through a per-warp shared-memory area,
+//                   string offsets.  No block barrier and no wait on other
+//                   warps, so the SM hides the latency of one warp's loads with
+//                   the others' work.
+//
+// Reading the code stream twice costs its bytes (about a fifth of the
+// traffic at 6 decoded bytes per 12-bit code) but removes the serial
+// look-back from the decode itself; this is the paper's sidecar (Sec. 3.1)
+// regenerated on the device by the first two passes.
+#pragma once
+#include "fp_decoder.cuh"
+
+namespace fp {
+namespace {
+
+// Warp-tile element <-> 64-bit word (bytes of a warp tile stay below 2^20).
+template <bool FSST>
+__device__ __forceinline__ u64 wt_pack(const TElem& e) {
+    if (!FSST) return e.b0;
+    return (u64)e.b0 | ((u64)e.b1 << 24) | ((u64)(e.n & 3u) << 48);
+}
+template <bool FSST>
+__device__ __forceinline__ Elem wt_unpack(u64 w) {
+    if (!FSST) return Elem{w, 0, 0};
+    return Elem{w & 0xffffffull, (w >> 24) & 0xffffffull, (u32)((w >> 48) & 3u)};
+}
+
+// Merge a partial chunk with the lead fragments of the following lanes of
+// the same warp tile and store it (the warp-tile form of combine_and_store).
+__device__ __forceinline__ void combine_lanes(uint4* chunk, uint4 acc, u32 lo, u32 hi, int m, const uint4* s_fa,
+                                              const u32* s_meta) {
+    while (hi < 16u && m < 32) {
+        const u32 mm = s_meta[m];
+        if (mm & FA_VALID) {
+            acc = or4(acc, s_fa[m]);
+            hi = (mm >> FA_HI_SHIFT) & 31u;
+        }
+        ++m;
+    }
+    if (lo == 0u && hi == 16u) __stcs(chunk, acc);
+    else store_partial(reinterpret_cast<uint8_t*>(chunk), acc, lo, hi);
+}
+
+// Per-warp shared-memory area of the decode kernel.
+template <int K>
+struct WarpArea {
+    uint4 fa[32];
+    uint4 fb[32];
+    u32 meta[32];
+    u32 thr_excl[32];       // tile-relative output offset of each lane
+    u32 contrib[K / 4][32]; // bytes each slot produced, one byte per slot
+    u32 lit_mask[32];       // FSST-8: bit k = slot k holds a literal byte
+};
+
+template <int CODEC, int K, bool DSMEM>
+struct WarpCore {
+    static constexpr bool FSST = (CODEC == FP_FSST8);
+    static constexpr int TILE = 32 * K;
+    static constexpr int WBITS = (CODEC == FP_ONPAIR16) ? 16 : (CODEC == FP_ONPAIR12 ? 12 : 8);
+    static constexpr int LANE_BYTES = K * WBITS / 8;   // code bytes of one lane
+    static constexpr int DICT_BYTES = DSMEM ? (FSST ? 256 * 8 : 4096 * 16) : 0;
+    static constexpr int LENS_BYTES = FSST ? 256 : (CODEC == FP_ONPAIR12 ? 4096 : 65536);
+    typedef TileRegs<CODEC, K> R;
+    static_assert(K == 8 || K == 16 || K == 32, "slots per lane");
+    static_assert(!FSST || K >= 16, "FSST-8 handles 16 slots at a time");
+    static_assert(!DSMEM || CODEC != FP_ONPAIR16, "OnPair-16 tables do not fit in shared memory");
+    static_assert(LANE_BYTES % 8 == 0, "lane code bytes are read in 8-byte words");
+
+    static __device__ __forceinline__ u32 full_mask() { return K == 32 ? 0xffffffffu : ((1u << K) - 1u); }
+
+    // ---- codes of slots [q0, q0 + K) ---------------------------------------
+    static __device__ __forceinline__ void unpack_words(const u32* wv, R& r) {
+        if (CODEC == FP_ONPAIR12) {
+#pragma unroll
+            for (int g = 0; g < K / 8; ++g) {
+                const u32 a = wv[3 * g], bb = wv[3 * g + 1], c = wv[3 * g + 2];
+                r.c[4 * g + 0] = (a & 0xfffu) | (((a >> 12) & 0xfffu) << 16);
+                r.c[4 * g + 1] = (__funnelshift_r(a, bb, 24) & 0xfffu) | (((bb >> 4) & 0xfffu) << 16);
+                r.c[4 * g + 2] = ((bb >> 16) & 0xfffu) | ((__funnelshift_r(bb, c, 28) & 0xfffu) << 16);
+                r.c[4 * g + 3] = ((c >> 8) & 0xfffu) | ((c >> 20) << 16);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < R::CW; ++m) r.c[m] = wv[m];
+        }
+    }
+
+    // Raw code words of the lane (LANE_BYTES / 4 words); false if the lane's
+    // bytes run past the buffer (then load_guarded() is used).
+    static __device__ __forceinline__ bool load_fast(const DecodeParams& p, u64 q0, u32 (&wv)[LANE_BYTES / 4]) {
+        const u64 b0 = q0 * WBITS / 8;   // q0 is a multiple of K, K a multiple of 8
+        if (b0 + LANE_BYTES > p.codes_bytes) return false;
+        if (LANE_BYTES % 16 == 0) {
+            const uint4* src = reinterpret_cast<const uint4*>(p.codes + b0);
+#pragma unroll
+            for (int v = 0; v < LANE_BYTES / 16; ++v) {
+                const uint4 a = __ldcs(src + v);
+                wv[4 * v] = a.x; wv[4 * v + 1] = a.y; wv[4 * v + 2] = a.z; wv[4 * v + 3] = a.w;
+            }
+        } else {
+            const uint2* src = reinterpret_cast<const uint2*>(p.codes + b0);
+#pragma unroll
+            for (int v = 0; v < LANE_BYTES / 8; ++v) {
+                const uint2 a = __ldcs(src + v);
+                wv[2 * v] = a.x; wv[2 * v + 1] = a.y;
+            }
+        }
+        return true;
+    }
+
+    static __device__ void load_guarded(const DecodeParams& p, u64 q0, R& r) {
+        if (CODEC == FP_ONPAIR16) {
+#pragma unroll
+            for (int m = 0; m < K / 2; ++m) {
+                u32 v = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const u64 q = q0 + 2 * m + h;
+                    if (q < p.max_slots) v |= ((u32)p.codes[2 * q] | ((u32)p.codes[2 * q + 1] << 8)) << (16 * h);
+                }
+                r.c[m] = v;
+            }
+        } else if (CODEC == FP_ONPAIR12) {
+#pragma unroll
+            for (int m = 0; m < K / 2; ++m) {
+                u32 v = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const u64 q = q0 + 2 * m + h;
+                    if (q < p.max_slots) {
+                        const u64 by = q * 3 / 2;
+                        const u32 lo8 = p.codes[by], hi8 = p.codes[by + 1];
+                        const u32 c = (q & 1) ? ((lo8 >> 4) | (hi8 << 4)) : (lo8 | ((hi8 & 0xfu) << 8));
+                        v |= c << (16 * h);
+                    }
+                }
+                r.c[m] = v;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < K / 4; ++m) {
+                u32 v = 0;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const u64 q = q0 + 4 * m + h;
+                    if (q < p.max_slots) v |= (u32)p.codes[q] << (8 * h);
+                }
+                r.c[m] = v;
+            }
+        }
+    }
+
+    // Codes (from words load_fast() fetched, or guarded loads), the slots
+    // inside the column and their token lengths.
+    static __device__ __forceinline__ void finish_load(const DecodeParams& p, const Extent& x, u64 q0,
+                                                       const u32 (&wv)[LANE_BYTES / 4], bool fast, const uint8_t* lens,
+                                                       R& r) {
+        if (fast) unpack_words(wv, r);
+        else load_guarded(p, q0, r);
+        if (q0 >= x.c_begin && q0 + K <= x.c_end) {
+            r.valid = full_mask();
+        } else {
+            u32 v = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const u64 q = q0 + k;
+                v |= ((q >= x.c_begin && q < x.c_end) ? 1u : 0u) << k;
+            }
+            r.valid = v;
+        }
+#pragma unroll
+        for (int j = 0; j < K / 4; ++j) {
+            u32 w = 0;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const u32 code = code_at<CODEC, K>(r, 4 * j + h);
+                const u32 L = DSMEM ? (u32)lens[code] : (u32)__ldg(lens + code);
+                w |= L << (8 * h);
+            }
+            r.L[j] = w;
+        }
+    }
+
+    // FSST-8 helpers on the lane's registers.
+    static __device__ __forceinline__ u32 ff_mask(const R& r) {
+        u32 E = 0;
+#pragma unroll
+        for (int j = 0; j < K / 4; ++j) E |= ff_bits4(r.c[j]) << (4 * j);
+        return E;
+    }
+    static __device__ __forceinline__ u32 fsst_bytes(const R& r, u32 codes, u32 lits) {
+        u32 n = __popc(lits);
+#pragma unroll
+        for (int j = 0; j < K / 4; ++j) n += byte_sum(r.L[j] & bytes_of4(codes >> (4 * j)));
+        return n;
+    }
+
+    // The lane's scan element; corrupt codes set ERRB_CORRUPT in err.
+    static __device__ __forceinline__ TElem element(const R& r, u32& err) {
+        const bool allv = (r.valid == full_mask());
+        if (!FSST) {
+            u32 sum = 0;
+            if (allv) {
+                bool zero = false;
+#pragma unroll
+                for (int j = 0; j < K / 4; ++j) {
+                    sum += byte_sum(r.L[j]);
+                    zero |= has_zero_byte(r.L[j]);
+                }
+                if (zero) err |= ERRB_CORRUPT;
+            } else {
+#pragma unroll
+                for (int j = 0; j < K / 4; ++j) {
+                    const u32 vm = bytes_of4(r.valid >> (4 * j));
+                    sum += byte_sum(r.L[j] & vm);
+                    if (__vcmpeq4(r.L[j], 0u) & vm) err |= ERRB_CORRUPT;
+                }
+            }
+            return TElem{sum, 0u, 0u};
+        }
+        if (allv) {
+            const u32 E = ff_mask(r);
+            u32 lit0, esc0, lit1, esc1;
+            fsst_escapes<K>(E, 0u, lit0, esc0);
+            fsst_escapes<K>(E, 1u, lit1, esc1);
+            const u32 c0 = fsst_bytes(r, ~(lit0 | esc0) & full_mask(), lit0);
+            const u32 c1 = fsst_bytes(r, ~(lit1 | esc1) & full_mask(), lit1);
+            return TElem{c0, c1, ((esc0 >> (K - 1)) & 1u) | (((esc1 >> (K - 1)) & 1u) << 1)};
+        }
+        // slots outside the column reset the state (the column starts on a code)
+        u32 c0 = 0, c1 = 0, s0 = 0, s1 = 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool v = (r.valid >> k) & 1u;
+            const u32 bt = code_at<CODEC, K>(r, k);
+            const u32 L = len_at<CODEC, K>(r, k);
+            const bool is255 = (bt == 255u);
+            const u32 a0 = s0 ? 1u : (is255 ? 0u : L);
+            const u32 n0 = s0 ? 0u : (is255 ? 1u : 0u);
+            const u32 a1 = s1 ? 1u : (is255 ? 0u : L);
+            const u32 n1 = s1 ? 0u : (is255 ? 1u : 0u);
+            c0 += v ? a0 : 0u;
+            c1 += v ? a1 : 0u;
+            s0 = v ? n0 : 0u;
+            s1 = v ? n1 : 0u;
+        }
+        return TElem{c0, c1, s0 | (s1 << 1)};
+    }
+
+    template <bool ALLV>
+    static __device__ __forceinline__ void assemble_onpair(const DecodeParams& p, const uint4* dict, const R& r,
+                                                           Assembler& as) {
+#pragma unroll
+        for (int k0 = 0; k0 < K; k0 += 4) {
+            uint4 tok[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const u32 code = code_at<CODEC, K>(r, k0 + h);
+                if (DSMEM) tok[h] = dict[code];
+                else tok[h] = __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int k = k0 + h;
+                if (ALLV) {
+                    as.put(tok[h], len_at<CODEC, K>(r, k));
+                } else {
+                    const bool v = (r.valid >> k) & 1u;
+                    as.put(v ? tok[h] : make_uint4(0, 0, 0, 0), v ? len_at<CODEC, K>(r, k) : 0u);
+                }
+            }
+        }
+    }
+
+    static __device__ __forceinline__ u64 lane_q0(const Extent& x, u64 t) {
+        return (x.first_tile + t) * (u64)TILE + (u64)(threadIdx.x & 31u) * K;
+    }
+
+    // Inputs of a warp tile fetched ahead of its decode: the lane's code
+    // words, the tile's scanned offset, its string boundaries [lo, hi) and
+    // the first PB*32 of their code_offsets (one per lane and round).
+    static constexpr int PB = FSST ? 2 : 1;
+    struct Fetch {
+        u32 wv[LANE_BYTES / 4];
+        bool fast;
+        u64 ex;
+        u32 lo, hi;
+        u32 pos[PB];
+    };
+
+    // Issue the loads of tile t whose boundaries [lo, hi) are already known.
+    static __device__ __forceinline__ void fetch(const DecodeParams& p, const Extent& x, const u64* ex, u64 t, u32 lo,
+                                                 u32 hi, Fetch& f) {
+        const u32 lane = threadIdx.x & 31u;
+        f.fast = load_fast(p, lane_q0(x, t), f.wv);
+        f.ex = __ldg(ex + t);
+        f.lo = lo;
+        f.hi = hi;
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+            const u32 i = lo + lane + 32u * j;
+            f.pos[j] = i < hi ? __ldg(p.code_offsets + i) : 0u;
+        }
+    }
+
+    // Boundaries [lo, hi) of tile t, clamped to the column's.
+    static __device__ __forceinline__ void bounds(const DecodeParams& p, u64 t, u32& lo, u32& hi) {
+        const u64 nb = (u64)p.n_strings + 1;
+        lo = __ldg(p.first + t);
+        hi = __ldg(p.first + t + 1);
+        if ((u64)lo > nb) lo = (u32)nb;
+        if ((u64)hi > nb) hi = (u32)nb;
+        if (hi < lo) hi = lo;
+    }
+
+    // Decode warp tile t of column (p, x) from its fetched inputs: offset
+    // and entering escape state (from the tile scan), code words, string
+    // boundaries.  `area` is the warp's scratch.
+    static __device__ __forceinline__ void decode_tile(const DecodeParams& p, const Extent& x, u64 t, const Fetch& f,
+                                                       const uint4* dict, const uint8_t* lens, WarpArea<K>& area,
+                                                       u32& err) {
+        const u32 lane = threadIdx.x & 31u;
+        const u64 tile_start = (x.first_tile + t) * (u64)TILE;
+        const u64 q0 = tile_start + (u64)lane * K;
+        const u64 ex = f.ex;
+        R r;
+        finish_load(p, x, q0, f.wv, f.fast, lens, r);
+        r.t = (u32)t;
+        r.tile_start = tile_start;
+        const bool allv = (r.valid == full_mask());
+        const TElem e = element(r, err);
+        const TElem ident = telem_identity();
+        const TElem inc = warp_scan_incl<FSST>(e, lane, ident);
+        TElem lex = shfl_up_e<FSST>(inc, 1);
+        if (lane == 0) lex = ident;
+        const TElem tot = shfl_e<FSST>(inc, 31);
+
+        const u64 tile_excl = ex & 0x7fffffffffffffffull;
+        const u32 s_tile = FSST ? (u32)(ex >> 63) : 0u;
+        const u64 tile_incl = tile_excl + ((FSST && s_tile) ? tot.b1 : tot.b0);
+        const u32 tile_out_state = FSST ? ((tot.n >> s_tile) & 1u) : 0u;
+        const u32 s_in = FSST ? ((lex.n >> s_tile) & 1u) : 0u;
+        const u32 thr = (FSST && s_tile) ? lex.b1 : lex.b0;
+        const bool last_tile = (t == x.n_tiles - 1);
+        const bool skip = p.size_only || tile_incl > p.capacity;
+
+        Assembler as;
+        as.begin(p.out, tile_excl + thr);
+        u32 produced = 0;
+        if (!FSST) {
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                const u32 cw = allv ? r.L[j] : (r.L[j] & bytes_of4(r.valid >> (4 * j)));
+                area.contrib[j][lane] = cw;
+                produced += byte_sum(cw);
+            }
+            if (!skip) {
+                if (allv) assemble_onpair<true>(p, dict, r, as);
+                else assemble_onpair<false>(p, dict, r, as);
+            }
+        } else {
+            u32 lit = 0;
+            u32 cw[K / 4];
+            if (allv) {
+                u32 esc;
+                fsst_escapes<K>(ff_mask(r), s_in, lit, esc);
+                const u32 code_slots = ~(lit | esc) & full_mask();
+#pragma unroll
+                for (int j = 0; j < K / 4; ++j) {
+                    cw[j] = (r.L[j] & bytes_of4(code_slots >> (4 * j))) | (bytes_of4(lit >> (4 * j)) & 0x01010101u);
+                    if (has_zero_byte(r.L[j] | ~bytes_of4(code_slots >> (4 * j)))) err |= ERRB_CORRUPT;
+                    produced += byte_sum(cw[j]);
+                }
+            } else {
+                u32 st = s_in;
+#pragma unroll
+                for (int j = 0; j < K / 4; ++j) cw[j] = 0u;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const bool v = (r.valid >> k) & 1u;
+                    const u32 bt = code_at<CODEC, K>(r, k);
+                    lit |= (st & 1u) << k;
+                    u32 a = 0;
+                    if (v) {
+                        if (st) { a = 1u; st = 0u; }
+                        else if (bt == 255u) { st = 1u; }
+                        else {
+                            a = len_at<CODEC, K>(r, k);
+                            if (a == 0u) err |= ERRB_CORRUPT;
+                        }
+                    } else {
+                        st = 0u;
+                    }
+                    cw[k >> 2] |= a << ((k & 3) * 8);
+                    produced += a;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) area.contrib[j][lane] = cw[j];
+            area.lit_mask[lane] = lit;
+            if (!skip) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const u32 bt = code_at<CODEC, K>(r, k);
+                    const u32 a = (cw[k >> 2] >> ((k & 3) * 8)) & 0xffu;
+                    const bool is_lit = (lit >> k) & 1u;
+                    uint2 d;
+                    if (DSMEM) d = reinterpret_cast<const uint2*>(dict)[bt];
+                    else d = __ldg(reinterpret_cast<const uint2*>(p.dict.table) + bt);
+                    const uint4 tok =
+                        make_uint4(a == 0u ? 0u : (is_lit ? bt : d.x), (a == 0u || is_lit) ? 0u : d.y, 0u, 0u);
+                    as.put(tok, a);
+                }
+            }
+        }
+        area.thr_excl[lane] = thr;
+        as.finish(produced > 0u && !skip);
+        area.fa[lane] = as.fa;
+        area.fb[lane] = as.fb;
+        area.meta[lane] = as.meta;
+        __syncwarp();
+
+        // chunks shared between lanes
+        if (!skip && produced > 0u) {
+            if (as.meta & FB_VALID)
+                combine_lanes(as.dst, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta);
+            if ((as.meta & FA_VALID) && thr == 0u)
+                combine_lanes(as.dst0, as.fa, (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
+                              (int)lane + 1, area.fa, area.meta);
+        }
+
+        // offsets of the strings whose boundaries the tile owns (the first
+        // PB*32 positions were fetched with the tile)
+        for (u32 i = f.lo + lane, j = 0; i < f.hi; i += 32, ++j) {
+            u64 pos;
+            if (j < (u32)PB) {
+                u32 v = f.pos[0];
+#pragma unroll
+                for (int m = 1; m < PB; ++m)
+                    if (j == (u32)m) v = f.pos[m];
+                pos = v;
+            } else {
+                pos = __ldg(p.code_offsets + i);
+            }
+            u64 rel = 0;
+            u32 st = 0;
+            if (pos < tile_start || pos > tile_start + TILE) {
+                err |= ERRB_CORRUPT;
+            } else if (pos == tile_start + TILE) {
+                rel = tile_incl - tile_excl;
+                st = tile_out_state;
+                if (!last_tile) err |= ERRB_CORRUPT;
+            } else {
+                const u32 sidx = (u32)(pos - tile_start);
+                const u32 j = sidx / K, k = sidx % K;
+                u32 acc = area.thr_excl[j];
+#pragma unroll
+                for (int m = 0; m < K / 4; ++m) {
+                    const u32 w = area.contrib[m][j];
+                    u32 keep = 0u;
+                    if ((u32)m < k / 4) keep = 0xffffffffu;
+                    else if ((u32)m == k / 4 && (k & 3u)) keep = 0xffffffffu >> (32 - 8 * (k & 3u));
+                    acc += byte_sum(w & keep);
+                }
+                rel = acc;
+                if (FSST) st = (area.lit_mask[j] >> k) & 1u;
+            }
+            if (st) err |= ERRB_CORRUPT;   // a string would start on a literal
+            if (!p.size_only) __stcs(p.out_offsets + i, (u32)(tile_excl + rel));
+        }
+        __syncwarp();   // the area is reused by the next tile
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Pass 1: warp-tile elements.
+// ---------------------------------------------------------------------------
+template <int CODEC, int K, bool DSMEM>
+__global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, const Extent* xp, u64* agg) {
+    typedef WarpCore<CODEC, K, DSMEM> C;
+    __shared__ __align__(16) uint8_t s_lens[DSMEM ? C::LENS_BYTES : 16];
+    if (DSMEM) {
+        const uint4* src = reinterpret_cast<const uint4*>(p.dict.lens);
+        for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += blockDim.x) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(src + i);
+        __syncthreads();
+    }
+    const Extent x = *xp;
+    const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
+    const u32 lane = threadIdx.x & 31u;
+    const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
+    u32 err = 0;
+    // rounds of U tiles; the next round's loads are in flight while this one computes
+    constexpr int U = 2;
+    u64 t0 = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    u32 wv[U][C::LANE_BYTES / 4];
+    bool fast[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const u64 t = t0 + u * warps;
+        fast[u] = t < x.n_tiles && C::load_fast(p, C::lane_q0(x, t), wv[u]);
+    }
+    for (; t0 < x.n_tiles; t0 += U * warps) {
+        u32 nv[U][C::LANE_BYTES / 4];
+        bool nfast[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u64 t = t0 + (U + u) * warps;
+            nfast[u] = t < x.n_tiles && C::load_fast(p, C::lane_q0(x, t), nv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u64 t = t0 + u * warps;
+            if (t < x.n_tiles) {
+                typename C::R r;
+                C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r);
+                const TElem e = C::element(r, err);
+                const TElem inc = warp_scan_incl<C::FSST>(e, lane, telem_identity());
+                if (lane == 31) agg[t] = wt_pack<C::FSST>(inc);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int i = 0; i < C::LANE_BYTES / 4; ++i) wv[u][i] = nv[u][i];
+            fast[u] = nfast[u];
+        }
+    }
+    if (err) atomicOr(p.err_word, err);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: exclusive scan of the warp-tile elements.  Blocks of 256 threads
+// take 2,048 consecutive elements by ticket; decoupled look-back across
+// blocks.  Writes ex[t] = bytes before warp tile t | entering state << 63.
+// ---------------------------------------------------------------------------
+constexpr int kScanPerThread = 8;
+constexpr int kScanTile = 256 * kScanPerThread;
+
+template <bool FSST>
+__global__ void __launch_bounds__(256) tiles_scan_kernel(const DecodeParams p, const Extent* xp, const u64* agg,
+                                                         u64* ex, unsigned long long* status) {
+    __shared__ Elem s_wsum[8];
+    __shared__ u64 s_excl_b;
+    __shared__ u32 s_excl_s;
+    __shared__ u32 s_ticket;
+    WsHeader* ws = p.ws;
+    const Extent x = *xp;
+    const u32 epoch = *(volatile u32*)&ws->epoch;
+    const u32 lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const u64 n = x.n_tiles;
+    const u64 n_blocks = (n + kScanTile - 1) / kScanTile;
+    const u64 pad = FSST ? wt_pack<true>(telem_identity()) : 0ull;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&ws->tile_counter, 1u);
+        __syncthreads();
+        const u64 b = s_ticket;
+        if (b >= n_blocks) break;
+        const u64 i0 = b * kScanTile + (u64)threadIdx.x * kScanPerThread;
+        u64 w[kScanPerThread];
+#pragma unroll
+        for (int k = 0; k < kScanPerThread; ++k) w[k] = (i0 + k < n) ? agg[i0 + k] : pad;
+        // this thread's elements composed, then a block scan of 64-bit elements
+        Elem e = elem_identity();
+#pragma unroll
+        for (int k = 0; k < kScanPerThread; ++k) e = then<FSST>(e, wt_unpack<FSST>(w[k]));
+        Elem inc = e;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            Elem y = shfl_up_e<FSST>(inc, d);
+            if (lane < (u32)d) y = elem_identity();
+            inc = then<FSST>(y, inc);
+        }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        Elem wex = elem_identity(), tot = elem_identity();
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const Elem sv = s_wsum[v];
+            if ((u32)v < warp) wex = then<FSST>(wex, sv);
+            tot = then<FSST>(tot, sv);
+        }
+        Elem lex = shfl_up_e<FSST>(inc, 1);
+        if (lane == 0) lex = elem_identity();
+        lex = then<FSST>(wex, lex);   // the block's elements before this thread's
+        if (warp == 0) {
+            // publish the aggregate first, so later blocks need not wait for this look-back
+            if (b > 0 && lane == 0) st_volatile(status + b, status_word(kFlagAgg, epoch, agg_payload_wide<FSST>(tot)));
+            u64 eb = 0;
+            u32 es = 0;
+            if (b > 0) lookback<FSST, true>(status, (long long)b, epoch, ws, eb, es);
+            if (lane == 0) {
+                const u64 ib = eb + ((FSST && es) ? tot.b1 : tot.b0);
+                const u32 is = FSST ? ((tot.n >> es) & 1u) : 0u;
+                st_volatile(status + b, status_word(kFlagInc, epoch, inc_payload<FSST>(ib, is)));
+                s_excl_b = eb;
+                s_excl_s = es;
+                if (b == n_blocks - 1) {
+                    *p.total_out = ib;
+                    if (ib > p.capacity && !p.size_only) atomicOr(p.err_word, ERRB_CAPACITY);
+                    if (ib > 0x7fffffffull) atomicOr(p.err_word, ERRB_OVERFLOW);
+                }
+            }
+        }
+        __syncthreads();
+        const u64 eb = s_excl_b;
+        const u32 es = s_excl_s;
+        // each element's exclusive offset and entering state
+        u64 ob = eb + ((FSST && es) ? lex.b1 : lex.b0);
+        u32 os = FSST ? ((lex.n >> es) & 1u) : 0u;
+#pragma unroll
+        for (int k = 0; k < kScanPerThread; ++k) {
+            if (i0 + k < n) ex[i0 + k] = ob | ((u64)os << 63);
+            const Elem ek = wt_unpack<FSST>(w[k]);
+            ob += (FSST && os) ? ek.b1 : ek.b0;
+            os = FSST ? ((ek.n >> os) & 1u) : 0u;
+        }
+        __syncthreads();   // shared words are rewritten for the next ticket
+    }
+    finish_launch(ws, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: every warp decodes warp tiles on its own (grid-stride order).
+// ---------------------------------------------------------------------------
+template <int CODEC, int K, bool DSMEM, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const DecodeParams p, const Extent* xp,
+                                                                     const u64* ex) {
+    typedef WarpCore<CODEC, K, DSMEM> C;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint4* s_dict = reinterpret_cast<uint4*>(smem_raw);
+    uint8_t* s_lens = smem_raw + C::DICT_BYTES;
+    WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
+    if (DSMEM) {
+        const uint4* src = reinterpret_cast<const uint4*>(p.dict.table);
+        for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
+        const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
+        for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
+        __syncthreads();
+    }
+    const Extent x = *xp;
+    const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
+    WarpArea<K>& area = areas[threadIdx.x >> 5];
+    const u64 warps = (u64)gridDim.x * NW;
+    u32 err = 0;
+    u64 t = (u64)blockIdx.x * NW + (threadIdx.x >> 5);
+    if (t < x.n_tiles) {
+        // Software pipeline: while tile t decodes, the inputs of t + warps are
+        // in flight and the boundaries of t + 2 * warps are being read.
+        typename C::Fetch cur;
+        u32 lo, hi, lo1 = 0, hi1 = 0;
+        C::bounds(p, t, lo, hi);
+        C::fetch(p, x, ex, t, lo, hi, cur);
+        if (t + warps < x.n_tiles) C::bounds(p, t + warps, lo1, hi1);
+        for (; t < x.n_tiles; t += warps) {
+            typename C::Fetch nxt;
+            const u64 tn = t + warps, t2 = t + 2 * warps;
+            u32 lo2 = 0, hi2 = 0;
+            if (tn < x.n_tiles) C::fetch(p, x, ex, tn, lo1, hi1, nxt);
+            if (t2 < x.n_tiles) C::bounds(p, t2, lo2, hi2);
+            C::decode_tile(p, x, t, cur, s_dict, lens, area, err);
+            cur = nxt;
+            lo1 = lo2;
+            hi1 = hi2;
+        }
+    }
+    if (err) atomicOr(p.err_word, err);
+}
+
+// Extent of the column for warp tiles (computed once on the device).
+__global__ void extent_kernel(const DecodeParams p, u64 tile, Extent* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = column_extent(p, tile);
+}
+
+}  // namespace
+}  // namespace fp
