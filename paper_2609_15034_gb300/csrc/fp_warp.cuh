@@ -39,10 +39,20 @@ __device__ __forceinline__ Elem wt_unpack(u64 w) {
     return Elem{w & 0xffffffull, (w >> 24) & 0xffffffull, (u32)((w >> 48) & 3u)};
 }
 
+// A chunk of which only bytes [lo, hi) may be written (shared with a
+// neighbouring warp tile).
+struct Partial {
+    uint4 v;
+    uint4* chunk;
+    u32 lo, hi;
+    bool pending;
+};
+
 // Merge a partial chunk with the lead fragments of the following lanes of
-// the same warp tile and store it (the warp-tile form of combine_and_store).
+// the same warp tile; store it if it is complete, else leave it pending for
+// store_partials().
 __device__ __forceinline__ void combine_lanes(uint4* chunk, uint4 acc, u32 lo, u32 hi, int m, const uint4* s_fa,
-                                              const u32* s_meta) {
+                                              const u32* s_meta, Partial& pend) {
     while (hi < 16u && m < 32) {
         const u32 mm = s_meta[m];
         if (mm & FA_VALID) {
@@ -51,8 +61,33 @@ __device__ __forceinline__ void combine_lanes(uint4* chunk, uint4 acc, u32 lo, u
         }
         ++m;
     }
-    if (lo == 0u && hi == 16u) __stcs(chunk, acc);
-    else store_partial(reinterpret_cast<uint8_t*>(chunk), acc, lo, hi);
+    if (lo == 0u && hi == 16u) {
+        __stcs(chunk, acc);
+    } else {
+        pend.v = acc;
+        pend.chunk = chunk;
+        pend.lo = lo;
+        pend.hi = hi;
+        pend.pending = true;
+    }
+}
+
+// The warp writes its lanes' pending partial chunks together: lane b stores
+// byte b of a chunk when b is in [lo, hi), one byte store per chunk.
+__device__ __forceinline__ void store_partials(const Partial& pd) {
+    const u32 lane = threadIdx.x & 31u;
+    u32 ball = __ballot_sync(0xffffffffu, pd.pending);
+    while (ball) {
+        const int src = __ffs(ball) - 1;
+        ball &= ball - 1u;
+        const u32 x = __shfl_sync(0xffffffffu, pd.v.x, src), y = __shfl_sync(0xffffffffu, pd.v.y, src);
+        const u32 z = __shfl_sync(0xffffffffu, pd.v.z, src), w = __shfl_sync(0xffffffffu, pd.v.w, src);
+        const u32 lo = __shfl_sync(0xffffffffu, pd.lo, src), hi = __shfl_sync(0xffffffffu, pd.hi, src);
+        const unsigned long long a = __shfl_sync(0xffffffffu, (unsigned long long)pd.chunk, src);
+        const u32 q = lane >> 2;
+        const u32 word = q == 0 ? x : (q == 1 ? y : (q == 2 ? z : w));
+        if (lane >= lo && lane < hi) reinterpret_cast<uint8_t*>(a)[lane] = (uint8_t)(word >> ((lane & 3u) * 8u));
+    }
 }
 
 // Per-warp shared-memory area of the decode kernel.
@@ -74,6 +109,7 @@ struct WarpCore {
     static constexpr int LANE_BYTES = K * WBITS / 8;   // code bytes of one lane
     static constexpr int DICT_BYTES = DSMEM ? (FSST ? 256 * 8 : 4096 * 16) : 0;
     static constexpr int LENS_BYTES = FSST ? 256 : (CODEC == FP_ONPAIR12 ? 4096 : 65536);
+    static constexpr int kTable = FSST ? 256 : 4096;   // entries of a table staged in shared memory
     typedef TileRegs<CODEC, K> R;
     static_assert(K == 8 || K == 16 || K == 32, "slots per lane");
     static_assert(!FSST || K >= 16, "FSST-8 handles 16 slots at a time");
@@ -270,8 +306,16 @@ struct WarpCore {
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const u32 code = code_at<CODEC, K>(r, k0 + h);
-                if (DSMEM) tok[h] = dict[code];
-                else tok[h] = __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
+                if (DSMEM) {
+                    // split read: the low 8 bytes always, the high 8 only for longer tokens
+                    const uint2* lo = reinterpret_cast<const uint2*>(dict);
+                    const uint2 a = lo[code];
+                    uint2 b = make_uint2(0u, 0u);
+                    if (len_at<CODEC, K>(r, k0 + h) > 8u) b = lo[kTable + code];
+                    tok[h] = make_uint4(a.x, a.y, b.x, b.y);
+                } else {
+                    tok[h] = __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
+                }
             }
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -434,14 +478,19 @@ struct WarpCore {
         area.meta[lane] = as.meta;
         __syncwarp();
 
-        // chunks shared between lanes
-        if (!skip && produced > 0u) {
-            if (as.meta & FB_VALID)
-                combine_lanes(as.dst, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta);
-            if ((as.meta & FA_VALID) && thr == 0u)
-                combine_lanes(as.dst0, as.fa, (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
-                              (int)lane + 1, area.fa, area.meta);
-        }
+        // chunks shared between lanes; the tile's edge chunks, shared with
+        // the neighbouring tiles, are written bytewise by the whole warp
+        const bool wrote = !skip && produced > 0u;
+        Partial pd;
+        pd.pending = false;
+        if (wrote && (as.meta & FB_VALID))
+            combine_lanes(as.dst, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
+        store_partials(pd);
+        pd.pending = false;
+        if (wrote && (as.meta & FA_VALID) && thr == 0u)
+            combine_lanes(as.dst0, as.fa, (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
+                          (int)lane + 1, area.fa, area.meta, pd);
+        store_partials(pd);
 
         // offsets of the strings whose boundaries the tile owns (the first
         // PB*32 positions were fetched with the tile)
@@ -646,7 +695,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
     WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
     if (DSMEM) {
         const uint4* src = reinterpret_cast<const uint4*>(p.dict.table);
-        for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
+        if (C::FSST) {
+            for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
+        } else {
+            // OnPair: entry e's bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e
+            uint2* planes = reinterpret_cast<uint2*>(s_dict);
+            for (int i = threadIdx.x; i < C::kTable; i += NW * 32) {
+                const uint4 v = __ldg(src + i);
+                planes[i] = make_uint2(v.x, v.y);
+                planes[C::kTable + i] = make_uint2(v.z, v.w);
+            }
+        }
         const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
         for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
         __syncthreads();
