@@ -56,6 +56,19 @@ BATCH_METRIC = "decoded GB/s (batched decode of many chunks, inputs resident in 
 L2_BYTES = 126 * 1024 * 1024
 
 
+def combine_ranks(dist, total_ms: float, nbytes: float, device):
+    """Whole-job timing of replicas: the slowest rank's time and the bytes
+    all ranks decoded (no data-path collective; replicas are independent)."""
+    import torch
+    if dist is None:
+        return total_ms, nbytes
+    tt = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    bt = torch.tensor([nbytes], device=device, dtype=torch.float64)
+    dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(bt.item())
+
+
 def env_rank():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -270,15 +283,7 @@ def run_ours(args, rank, world, local_rank):
     st = fp.sync_status(sh)
     if st != fp.OK:
         raise RuntimeError(fp.last_error())
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        bt = torch.tensor([float(total)], device=dev, dtype=torch.float64)
-        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
-        all_bytes = float(bt.item())
-    else:
-        all_bytes = float(total)
+    total_ms, all_bytes = combine_ranks(dist, total_ms, float(total), dev)
 
     value = all_bytes * args.steps / (total_ms * 1e-3) / 1e9
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
@@ -525,14 +530,7 @@ def run_batched(args, rank, world, local_rank):
     st, sts, tot = plan.sync_status(sh)
     if st != fp.OK:
         raise RuntimeError(fp.last_error())
-    all_bytes = float(total)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        bt = torch.tensor([all_bytes], device=dev, dtype=torch.float64)
-        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
-        all_bytes = float(bt.item())
+    total_ms, all_bytes = combine_ranks(dist, total_ms, float(total), dev)
     value = all_bytes * args.steps / (total_ms * 1e-3) / 1e9
     avg_s = statistics.mean(launch_ms) * 1e-3
     alg = 0
