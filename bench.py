@@ -356,8 +356,8 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
-    var = fp.variant_selected(codec)
-    vinfo = fp.variant_info(codec, var)
+    var = fp.variant_for(codec, codes_bytes)
+    vinfo = dict(fp.variant_info(codec, var), index=var)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -373,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": load_traffic(args.workload), "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": round(avg_launch_s * 1e3, 4)},
         "clocks": clocks,
-        "gpu_launches": 2 * args.steps,   # per step: the index pass and the decode kernel
+        "gpu_launches": vinfo["launches_per_call"] * args.steps,   # index pass [+ reduce + tile scan] + decode
     }
     line.update(extra)
     if "e2e" not in line:

@@ -395,17 +395,25 @@ fp_status fp_serve_destroy(fp_server* server);
  * (shared memory staged once per block, or the L1/L2 cache path).
  *
  * fp_variant_count  number of compiled variants for a codec.
- * fp_variant_info   describe variant v: threads, slots per thread, 1 if the
- *                   dictionary is staged in shared memory.
+ * fp_variant_info   describe variant v: threads per block, slots per thread,
+ *                   1 if the dictionary is staged in shared memory, and the
+ *                   kernel launches of one fp_decode call (2: index pass and
+ *                   block-pipeline decode; 4: index pass, reduce, tile scan
+ *                   and warp-tile decode).  Any out pointer may be NULL.
  * fp_variant_select make variant v the one fp_decode uses for the codec in
- *                   this process (v = -1 restores the built-in default).
- * fp_variant_selected  the variant fp_decode currently uses for the codec.
+ *                   this process (v = -1 restores the built-in defaults,
+ *                   which depend on the size of the code buffer).
+ * fp_variant_selected  the variant selected for the codec, or with none
+ *                   selected the default for large code buffers.
+ * fp_variant_for    the variant fp_decode uses for a code buffer of
+ *                   codes_bytes bytes (-1 for an unknown codec).
  */
 int fp_variant_count(fp_codec codec);
 fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* slots_per_thread,
-                          uint32_t* dict_in_smem);
+                          uint32_t* dict_in_smem, uint32_t* launches_per_call);
 fp_status fp_variant_select(fp_codec codec, int v);
 int fp_variant_selected(fp_codec codec);
+int fp_variant_for(fp_codec codec, uint64_t codes_bytes);
 
 #ifdef __cplusplus
 }

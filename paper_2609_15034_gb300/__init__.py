@@ -61,9 +61,11 @@ def lib() -> ctypes.CDLL:
             L.fp_sync_status.argtypes = [P]
             L.fp_last_error.restype = ctypes.c_char_p
             L.fp_variant_count.argtypes = [I]
-            L.fp_variant_info.argtypes = [I, I, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32)]
+            L.fp_variant_info.argtypes = [I, I, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32),
+                                          ctypes.POINTER(U32)]
             L.fp_variant_select.argtypes = [I, I]
             L.fp_variant_selected.argtypes = [I]
+            L.fp_variant_for.argtypes = [I, U64]
             L.fp_plan_create.argtypes = [ctypes.POINTER(Chunk), U32, ctypes.c_char_p, P, ctypes.POINTER(P)]
             L.fp_plan_create_config.argtypes = [ctypes.POINTER(Chunk), U32, I, P, ctypes.POINTER(P)]
             L.fp_decode_batch.argtypes = [P, P]
@@ -233,9 +235,11 @@ def variant_count(codec: int) -> int:
 
 
 def variant_info(codec: int, v: int) -> dict:
-    t, k, s = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-    _check(lib().fp_variant_info(codec, v, ctypes.byref(t), ctypes.byref(k), ctypes.byref(s)), "fp_variant_info")
-    return {"threads": t.value, "slots_per_thread": k.value, "dict_in_smem": bool(s.value)}
+    t, k, s, n = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().fp_variant_info(codec, v, ctypes.byref(t), ctypes.byref(k), ctypes.byref(s), ctypes.byref(n)),
+           "fp_variant_info")
+    return {"threads": t.value, "slots_per_thread": k.value, "dict_in_smem": bool(s.value),
+            "warp_tiles": n.value == 4, "launches_per_call": n.value}
 
 
 def variant_select(codec: int, v: int) -> None:
@@ -244,6 +248,11 @@ def variant_select(codec: int, v: int) -> None:
 
 def variant_selected(codec: int) -> int:
     return lib().fp_variant_selected(codec)
+
+
+def variant_for(codec: int, codes_bytes: int) -> int:
+    """The variant fp_decode uses for a code buffer of codes_bytes bytes."""
+    return lib().fp_variant_for(codec, codes_bytes)
 
 
 # ---- torch conveniences (tensors are only carriers of device memory) -------

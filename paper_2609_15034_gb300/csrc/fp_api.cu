@@ -111,9 +111,10 @@ Workspace* find_workspace(cudaStream_t stream) {
 // ---- variants and occupancy ----------------------------------------------------
 std::atomic<int> g_selected[4] = {{-1}, {-1}, {-1}, {-1}};
 
-int selected_variant(int codec) {
+// The selected variant, else the default for a code buffer of max_slots.
+int selected_variant(int codec, uint64_t max_slots) {
     const int v = g_selected[codec].load();
-    return v >= 0 ? v : variant_default(codec);
+    return v >= 0 ? v : variant_default(codec, max_slots);
 }
 
 struct DevInfo {
@@ -211,10 +212,10 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
                      const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
                      uint64_t out_capacity, uint32_t* d_out_offsets, cudaStream_t stream, bool size_only,
                      Workspace** ws_out) {
-    const Variant* var = variant_get(codec, selected_variant(codec));
+    const uint64_t max_slots = max_slots_of(codec, codes_bytes);
+    const Variant* var = variant_get(codec, selected_variant(codec, max_slots));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
-    const uint64_t max_slots = max_slots_of(codec, codes_bytes);
     const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
     int per_wave = 0, sms = 0;
@@ -401,13 +402,14 @@ fp_status fp_sync_status(fp_stream_t stream_) {
 int fp_variant_count(fp_codec codec) { return valid_codec(codec) ? variant_count(codec) : 0; }
 
 fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* slots_per_thread,
-                          uint32_t* dict_in_smem) {
+                          uint32_t* dict_in_smem, uint32_t* launches_per_call) {
     if (!valid_codec(codec)) return fail(FP_ERR_ARG, "unknown codec %d", (int)codec);
     const Variant* var = variant_get(codec, v);
     if (!var) return fail(FP_ERR_ARG, "variant %d out of range", v);
     if (threads) *threads = (uint32_t)var->threads;
     if (slots_per_thread) *slots_per_thread = (uint32_t)var->slots_per_thread;
     if (dict_in_smem) *dict_in_smem = (uint32_t)var->dict_smem;
+    if (launches_per_call) *launches_per_call = var->warp_tiles ? 4u : 2u;
     return FP_OK;
 }
 
@@ -418,7 +420,11 @@ fp_status fp_variant_select(fp_codec codec, int v) {
     return FP_OK;
 }
 
-int fp_variant_selected(fp_codec codec) { return valid_codec(codec) ? selected_variant(codec) : -1; }
+int fp_variant_selected(fp_codec codec) { return valid_codec(codec) ? selected_variant(codec, 1ull << 32) : -1; }
+
+int fp_variant_for(fp_codec codec, uint64_t codes_bytes) {
+    return valid_codec(codec) ? selected_variant(codec, max_slots_of(codec, codes_bytes)) : -1;
+}
 
 }  // extern "C"
 
@@ -484,9 +490,9 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     if (st != FP_OK) return st;
     if (!d_status || reinterpret_cast<uintptr_t>(d_status) % 4) return fail(FP_ERR_ARG, "d_status must be a 4-byte aligned device pointer");
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
-    const Variant* var = variant_get(codec, selected_variant(codec));
-    if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     const uint64_t max_slots = max_slots_of(codec, codes_bytes);
+    const Variant* var = variant_get(codec, selected_variant(codec, max_slots));
+    if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
     const size_t need = variant_scratch_bytes(*var, max_slots);

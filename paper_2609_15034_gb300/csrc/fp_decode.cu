@@ -7,9 +7,12 @@
 namespace fp {
 namespace {
 
-// Index pass over one column (grid-stride over its string boundaries).
-__global__ void __launch_bounds__(256) index_kernel(const DecodeParams p, u32 tile, u32* first) {
+// Index pass over one column (grid-stride over its string boundaries);
+// block 0 also stores the column's extent for the later passes (xp may be
+// null).
+__global__ void __launch_bounds__(256) index_kernel(const DecodeParams p, u32 tile, u32* first, Extent* xp) {
     const Extent x = column_extent(p, tile);
+    if (xp && blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
     index_groups(p, x, (u32)(__ffsll((long long)tile) - 1), 0, (u64)p.n_strings + 1,
                  (u64)blockIdx.x * blockDim.x + threadIdx.x, (u64)gridDim.x * blockDim.x, first);
 }
@@ -93,12 +96,16 @@ const Variant* variant_get(int codec, int v) {
     return (t && v >= 0 && v < n) ? &t[v] : nullptr;
 }
 
-// Defaults chosen by measurement on GB300 (full-size synthetic columns):
+// Defaults chosen by measurement on GB300 (synthetic columns):
 // OnPair-12 warp tiles, 10 warps per block, dictionary in shared memory;
-// FSST-8 block pipeline with 32 slots per thread; OnPair-16 block pipeline.
-int variant_default(int codec) {
+// OnPair-16 warp tiles, 8 warps per block (dictionary through L1) for large
+// buffers (790 vs 551 GB/s at 10M strings) and the one-launch block pipeline
+// for small ones (220 vs 171 GB/s at 100k strings, where the warp tiles'
+// extra launches dominate); FSST-8 block pipeline with 32 slots per thread.
+int variant_default(int codec, uint64_t max_slots) {
     switch (codec) {
         case FP_ONPAIR12: return 5;
+        case FP_ONPAIR16: return max_slots >= (1ull << 23) ? 3 : 0;
         case FP_FSST8: return 1;
         default: return 0;
     }
@@ -157,19 +164,17 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
     const uint64_t nb = (uint64_t)p.n_strings + 1;
     uint64_t ib = (nb + 256 * kIdxGroup - 1) / (256 * kIdxGroup);
     if (ib > (uint64_t)sms * 8) ib = (uint64_t)sms * 8;
-    index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first);
+    index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first,
+                                                   var.warp_tiles ? reinterpret_cast<Extent*>(base + L.o_extent) : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&p};
     if (!var.warp_tiles) return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
 
-    // warp tiles: extent, reduce, tile scan, decode
+    // warp tiles: reduce, tile scan, decode (the index pass stored the extent)
     Extent* xp = reinterpret_cast<Extent*>(base + L.o_extent);
     u64* agg = reinterpret_cast<u64*>(base + L.o_agg);
     u64* ex = reinterpret_cast<u64*>(base + L.o_ex);
-    extent_kernel<<<1, 32, 0, stream>>>(p, tile, xp);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     const uint64_t n_wt_max = L.n_tiles;   // upper bound; the kernels read the true count from *xp
     uint64_t rg = (n_wt_max + 7) / 8;
     const uint64_t rg_cap = (uint64_t)sms * 8;

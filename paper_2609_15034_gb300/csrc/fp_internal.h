@@ -114,7 +114,7 @@ struct Variant {
 // Variant tables (fp_decode.cu).
 int variant_count(int codec);
 const Variant* variant_get(int codec, int v);
-int variant_default(int codec);
+int variant_default(int codec, uint64_t max_slots);   // default for a code buffer of max_slots slots
 
 // Launch helpers (fp_decode.cu, fp_plain.cu).
 uint64_t variant_tile(const Variant& v);   // code slots per tile (block tile or warp tile)

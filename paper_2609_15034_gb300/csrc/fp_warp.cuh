@@ -739,10 +739,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
     if (err) atomicOr(p.err_word, err);
 }
 
-// Extent of the column for warp tiles (computed once on the device).
-__global__ void extent_kernel(const DecodeParams p, u64 tile, Extent* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *out = column_extent(p, tile);
-}
 
 }  // namespace
 }  // namespace fp
