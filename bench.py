@@ -52,6 +52,7 @@ SERVE_WORKLOADS = {
 }
 METRIC = "decoded GB/s (single-column decode, inputs resident in HBM)"
 SERVE_METRIC = "served decode: aggregate decoded GB/s at the offered load, with p50/p99 latency"
+SERVE_DEFAULT_CONFIG = 3   # the library's default batch configuration (warp tiles)
 BATCH_METRIC = "decoded GB/s (batched decode of many chunks, inputs resident in HBM)"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -640,7 +641,8 @@ def run_batched(args, rank, world, local_rank):
                      "traffic": load_traffic(args.workload), "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": round(avg_s * 1e3, 4)},
         "clocks": clocks,
-        "gpu_launches": 2 * args.steps,   # per step: one graph = the index pass and the persistent decode kernel
+        # per step one graph: index pass [+ reduce + tile scan] + the persistent decode kernel
+        "gpu_launches": (4 if fp.batch_config_info(pinfo["config"])["warp_tiles"] else 2) * args.steps,
     }
     line.update(extra)
     if "e2e" not in line:
@@ -782,8 +784,9 @@ def run_served(args, rank, world, local_rank):
             codes = torch.from_numpy(np.ascontiguousarray(I.pools[c].stream[b0:b1])).to(dev)
             cot = torch.from_numpy(co.view(np.int32)).to(dev)
             page_dev[(c, j)] = (codes, cot, b1 - b0, co.size - 1, dec)
+    serve_cfg = args.serve_config if args.serve_config >= 0 else SERVE_DEFAULT_CONFIG
     srv = fp.Server(hbm_budget=budget, dict_cache_slots=512, n_streams=args.serve_streams,
-                    max_wave=args.serve_wave, batch_config=0)
+                    max_wave=args.serve_wave, batch_config=serve_cfg)
     for k, c in I.keys:
         d = I.dictionary(k)
         srv.dict_put(k, c, d.data, d.offsets)
@@ -1005,6 +1008,7 @@ def run_served(args, rank, world, local_rank):
         "config": {"workload": args.workload, "description": desc, "arrival_rate": rate, "seconds": seconds,
                    "requests": n_req, "decoded_bytes": tot_bytes, "offered_gbs": round(tot_bytes / seconds / 1e9, 2),
                    "late_submissions": late, "n_streams": args.serve_streams, "max_wave": args.serve_wave,
+                   "batch_config": serve_cfg,
                    "waves": waves, "mean_wave": round((st1["admitted"] - st0["admitted"]) / max(waves, 1), 2),
                    "dict_hits": st1["dict_hits"] - st0["dict_hits"],
                    "dict_misses": st1["dict_misses"] - st0["dict_misses"],
@@ -1012,7 +1016,8 @@ def run_served(args, rank, world, local_rank):
                    "generation_s": round(t_gen, 1), "parallelism": "single GPU",
                    "ms_per_step": "mean request latency"},
         "clocks": clocks,
-        "gpu_launches": 2 * waves,   # per wave: the index pass and the persistent decode kernel
+        # per wave: index pass [+ reduce + tile scan] + the persistent decode kernel
+        "gpu_launches": (4 if fp.batch_config_info(serve_cfg)["warp_tiles"] else 2) * waves,
     }
     line.update(extra)
     if "e2e" not in line:
@@ -1078,6 +1083,7 @@ def main():
     ap.add_argument("--serve-saturation", type=int, default=2000, help="served: requests of the closed-loop run")
     ap.add_argument("--serve-plain", type=int, default=500, help="served: requests of the per-request baselines")
     ap.add_argument("--serve-stall", type=float, default=60.0, help="served: give up after this long without a result")
+    ap.add_argument("--serve-config", type=int, default=-1, help="served: batch configuration of the waves (-1: default)")
     ap.add_argument("--serve-watchdog", type=float, default=300.0, help="served: dump thread stacks every N s")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -294,9 +294,14 @@ fp_status fp_plan_info(const fp_plan* plan, fp_plan_info_t* info);
 /* Release a plan (synchronises the device first).  NULL is a no-op. */
 fp_status fp_plan_destroy(fp_plan* plan);
 
-/* Batch configurations: slots per thread per codec and blocks per SM. */
+/* Batch configurations: slots per thread per codec (OnPair-16, OnPair-12,
+ * FSST-8), blocks per SM, and 1 for the warp-tile decoder (index pass,
+ * reduce, tile scan and a persistent decode: four launches) or 0 for the
+ * block pipeline (index pass and the persistent decode).  Out pointers may be
+ * NULL. */
 int fp_batch_config_count(void);
-fp_status fp_batch_config_info(int config, uint32_t* slots_per_thread3, uint32_t* blocks_per_sm);
+fp_status fp_batch_config_info(int config, uint32_t* slots_per_thread3, uint32_t* blocks_per_sm,
+                               uint32_t* warp_tiles);
 
 /*
  * ---------------------------------------------------------------------------
@@ -320,7 +325,8 @@ typedef struct fp_serve_config {
     uint32_t max_inflight;      /* admitted requests not yet decoded (0 = 4096) */
     uint32_t n_streams;         /* waves in flight at once (0 = 4) */
     uint32_t max_wave;          /* requests per wave (0 = 256) */
-    int32_t batch_config;       /* batch configuration of the waves (see fp_batch_config_info) */
+    int32_t batch_config;       /* batch configuration of the waves (fp_batch_config_info); negative:
+                                   the library's default */
     uint32_t reserved;
 } fp_serve_config;
 

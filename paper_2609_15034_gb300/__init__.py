@@ -72,7 +72,7 @@ def lib() -> ctypes.CDLL:
             L.fp_plan_sync_status.argtypes = [P, P, P, P]
             L.fp_plan_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
             L.fp_plan_destroy.argtypes = [P]
-            L.fp_batch_config_info.argtypes = [I, P, ctypes.POINTER(U32)]
+            L.fp_batch_config_info.argtypes = [I, P, ctypes.POINTER(U32), ctypes.POINTER(U32)]
             L.fp_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]
             L.fp_serve_dict_put.argtypes = [P, U64, I, P, P, U32]
             L.fp_serve_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(U64)]
@@ -348,10 +348,10 @@ def batch_config_count() -> int:
 
 def batch_config_info(config: int) -> dict:
     k = (ctypes.c_uint32 * 3)()
-    b = ctypes.c_uint32()
-    _check(lib().fp_batch_config_info(config, ctypes.cast(k, ctypes.c_void_p), ctypes.byref(b)),
+    b, w = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().fp_batch_config_info(config, ctypes.cast(k, ctypes.c_void_p), ctypes.byref(b), ctypes.byref(w)),
            "fp_batch_config_info")
-    return {"slots_per_thread": list(k), "blocks_per_sm": b.value}
+    return {"slots_per_thread": list(k), "blocks_per_sm": b.value, "warp_tiles": bool(w.value)}
 
 
 # ---- served decode (fp_serve_*) ----------------------------------------------
@@ -360,7 +360,7 @@ class Server:
     """fp_server: continuous-batching decode loop run by a library thread."""
 
     def __init__(self, hbm_budget: int, dict_cache_slots: int = 512, max_inflight: int = 4096, n_streams: int = 4,
-                 max_wave: int = 256, batch_config: int = 0):
+                 max_wave: int = 256, batch_config: int = -1):
         cfg = ServeConfig(hbm_budget, dict_cache_slots, max_inflight, n_streams, max_wave, batch_config, 0)
         h = ctypes.c_void_p()
         _check(lib().fp_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "fp_serve_create")

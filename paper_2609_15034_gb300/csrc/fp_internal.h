@@ -81,6 +81,10 @@ struct alignas(16) SlotSrc {
     Extent x;
     uint32_t tile_base;   // queue ticket of the chunk's first tile
     uint32_t chunk;       // index of the chunk in the plan
+    // warp-tile batches only
+    unsigned long long wt_base;   // index of the chunk's first warp tile in the batch's element arrays
+    uint32_t sb_base;             // the chunk's first tile-scan block (its look-back words start there)
+    uint32_t n_sb;                // the chunk's tile-scan blocks
 };
 static_assert(sizeof(SlotSrc) % 16 == 0, "chunk records are copied in 16-byte pieces");
 
@@ -96,6 +100,12 @@ struct BatchParams {
     WsHeader* ws;
     BatchQueue q[3];      // OnPair-16, OnPair-12, FSST-8
     uint32_t split[2];    // blocks [0, split[0]) start on queue 0, [split[0], split[1]) on 1, the rest on 2
+    // warp-tile batches only
+    unsigned long long* agg;        // scan element of every warp tile
+    unsigned long long* ex;         // scanned offset | entering state of every warp tile
+    const uint2* scan_blocks;       // (queue << 30 | chunk, block within the chunk) per tile-scan block
+    uint32_t n_scan_blocks;
+    uint32_t pad;
 };
 
 // A compiled decoder shape.

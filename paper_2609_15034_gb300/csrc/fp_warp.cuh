@@ -599,85 +599,100 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, co
 constexpr int kScanPerThread = 8;
 constexpr int kScanTile = 256 * kScanPerThread;
 
+// Shared state of a tile-scan block.
+struct ScanShared {
+    Elem wsum[8];
+    u64 excl_b;
+    u32 excl_s;
+    u32 ticket;
+};
+
+// Scan block b (of n_blocks) over elements agg[0, n) of one column: writes
+// ex[] for its 2,048 elements, publishes its look-back word in status[b]
+// (status words of this column only), and at the column's last block its
+// decoded size and size errors.  Every thread of the block calls this.
+template <bool FSST>
+__device__ __forceinline__ void scan_block(const DecodeParams& p, const u64* agg, u64* ex, u64 n, u64 b, u64 n_blocks,
+                                           unsigned long long* status, u32 epoch, WsHeader* ws, ScanShared& sh) {
+    const u32 lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const u64 pad = FSST ? wt_pack<true>(telem_identity()) : 0ull;
+    const u64 i0 = b * kScanTile + (u64)threadIdx.x * kScanPerThread;
+    u64 w[kScanPerThread];
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) w[k] = (i0 + k < n) ? agg[i0 + k] : pad;
+    // this thread's elements composed, then a block scan of 64-bit elements
+    Elem e = elem_identity();
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) e = then<FSST>(e, wt_unpack<FSST>(w[k]));
+    Elem inc = e;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        Elem y = shfl_up_e<FSST>(inc, d);
+        if (lane < (u32)d) y = elem_identity();
+        inc = then<FSST>(y, inc);
+    }
+    if (lane == 31) sh.wsum[warp] = inc;
+    __syncthreads();
+    Elem wex = elem_identity(), tot = elem_identity();
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const Elem sv = sh.wsum[v];
+        if ((u32)v < warp) wex = then<FSST>(wex, sv);
+        tot = then<FSST>(tot, sv);
+    }
+    Elem lex = shfl_up_e<FSST>(inc, 1);
+    if (lane == 0) lex = elem_identity();
+    lex = then<FSST>(wex, lex);   // the block's elements before this thread's
+    if (warp == 0) {
+        // publish the aggregate first, so later blocks need not wait for this look-back
+        if (b > 0 && lane == 0) st_volatile(status + b, status_word(kFlagAgg, epoch, agg_payload_wide<FSST>(tot)));
+        u64 eb = 0;
+        u32 es = 0;
+        if (b > 0) lookback<FSST, true>(status, (long long)b, epoch, ws, eb, es);
+        if (lane == 0) {
+            const u64 ib = eb + ((FSST && es) ? tot.b1 : tot.b0);
+            const u32 is = FSST ? ((tot.n >> es) & 1u) : 0u;
+            st_volatile(status + b, status_word(kFlagInc, epoch, inc_payload<FSST>(ib, is)));
+            sh.excl_b = eb;
+            sh.excl_s = es;
+            if (b == n_blocks - 1) {
+                *p.total_out = ib;
+                if (ib > p.capacity && !p.size_only) atomicOr(p.err_word, ERRB_CAPACITY);
+                if (ib > 0x7fffffffull) atomicOr(p.err_word, ERRB_OVERFLOW);
+            }
+        }
+    }
+    __syncthreads();
+    const u64 eb = sh.excl_b;
+    const u32 es = sh.excl_s;
+    // each element's exclusive offset and entering state
+    u64 ob = eb + ((FSST && es) ? lex.b1 : lex.b0);
+    u32 os = FSST ? ((lex.n >> es) & 1u) : 0u;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        if (i0 + k < n) ex[i0 + k] = ob | ((u64)os << 63);
+        const Elem ek = wt_unpack<FSST>(w[k]);
+        ob += (FSST && os) ? ek.b1 : ek.b0;
+        os = FSST ? ((ek.n >> os) & 1u) : 0u;
+    }
+    __syncthreads();   // shared words are rewritten for the next ticket
+}
+
 template <bool FSST>
 __global__ void __launch_bounds__(256) tiles_scan_kernel(const DecodeParams p, const Extent* xp, const u64* agg,
                                                          u64* ex, unsigned long long* status) {
-    __shared__ Elem s_wsum[8];
-    __shared__ u64 s_excl_b;
-    __shared__ u32 s_excl_s;
-    __shared__ u32 s_ticket;
+    __shared__ ScanShared sh;
     WsHeader* ws = p.ws;
     const Extent x = *xp;
     const u32 epoch = *(volatile u32*)&ws->epoch;
-    const u32 lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const u64 n = x.n_tiles;
     const u64 n_blocks = (n + kScanTile - 1) / kScanTile;
-    const u64 pad = FSST ? wt_pack<true>(telem_identity()) : 0ull;
     for (;;) {
-        if (threadIdx.x == 0) s_ticket = atomicAdd(&ws->tile_counter, 1u);
+        if (threadIdx.x == 0) sh.ticket = atomicAdd(&ws->tile_counter, 1u);
         __syncthreads();
-        const u64 b = s_ticket;
+        const u64 b = sh.ticket;
         if (b >= n_blocks) break;
-        const u64 i0 = b * kScanTile + (u64)threadIdx.x * kScanPerThread;
-        u64 w[kScanPerThread];
-#pragma unroll
-        for (int k = 0; k < kScanPerThread; ++k) w[k] = (i0 + k < n) ? agg[i0 + k] : pad;
-        // this thread's elements composed, then a block scan of 64-bit elements
-        Elem e = elem_identity();
-#pragma unroll
-        for (int k = 0; k < kScanPerThread; ++k) e = then<FSST>(e, wt_unpack<FSST>(w[k]));
-        Elem inc = e;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            Elem y = shfl_up_e<FSST>(inc, d);
-            if (lane < (u32)d) y = elem_identity();
-            inc = then<FSST>(y, inc);
-        }
-        if (lane == 31) s_wsum[warp] = inc;
-        __syncthreads();
-        Elem wex = elem_identity(), tot = elem_identity();
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            const Elem sv = s_wsum[v];
-            if ((u32)v < warp) wex = then<FSST>(wex, sv);
-            tot = then<FSST>(tot, sv);
-        }
-        Elem lex = shfl_up_e<FSST>(inc, 1);
-        if (lane == 0) lex = elem_identity();
-        lex = then<FSST>(wex, lex);   // the block's elements before this thread's
-        if (warp == 0) {
-            // publish the aggregate first, so later blocks need not wait for this look-back
-            if (b > 0 && lane == 0) st_volatile(status + b, status_word(kFlagAgg, epoch, agg_payload_wide<FSST>(tot)));
-            u64 eb = 0;
-            u32 es = 0;
-            if (b > 0) lookback<FSST, true>(status, (long long)b, epoch, ws, eb, es);
-            if (lane == 0) {
-                const u64 ib = eb + ((FSST && es) ? tot.b1 : tot.b0);
-                const u32 is = FSST ? ((tot.n >> es) & 1u) : 0u;
-                st_volatile(status + b, status_word(kFlagInc, epoch, inc_payload<FSST>(ib, is)));
-                s_excl_b = eb;
-                s_excl_s = es;
-                if (b == n_blocks - 1) {
-                    *p.total_out = ib;
-                    if (ib > p.capacity && !p.size_only) atomicOr(p.err_word, ERRB_CAPACITY);
-                    if (ib > 0x7fffffffull) atomicOr(p.err_word, ERRB_OVERFLOW);
-                }
-            }
-        }
-        __syncthreads();
-        const u64 eb = s_excl_b;
-        const u32 es = s_excl_s;
-        // each element's exclusive offset and entering state
-        u64 ob = eb + ((FSST && es) ? lex.b1 : lex.b0);
-        u32 os = FSST ? ((lex.n >> es) & 1u) : 0u;
-#pragma unroll
-        for (int k = 0; k < kScanPerThread; ++k) {
-            if (i0 + k < n) ex[i0 + k] = ob | ((u64)os << 63);
-            const Elem ek = wt_unpack<FSST>(w[k]);
-            ob += (FSST && os) ? ek.b1 : ek.b0;
-            os = FSST ? ((ek.n >> os) & 1u) : 0u;
-        }
-        __syncthreads();   // shared words are rewritten for the next ticket
+        scan_block<FSST>(p, agg, ex, n, b, n_blocks, status, epoch, ws, sh);
     }
     finish_launch(ws, epoch);
 }
