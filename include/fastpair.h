@@ -192,10 +192,11 @@ const char* fp_last_error(void);
  *              wait gave up.  fp_sync_status does not report these calls.
  *
  * Limits and sharing:
- *   - the code buffer may span at most the tiles the scratch holds
- *     (87,370 tiles minus 2: about 357M slots with the default tile of 4,096
- *     slots); larger inputs return FP_ERR_ARG with the limit in
- *     fp_last_error() -- use fp_decode for them.
+ *   - unless a variant is selected (fp_variant_select), this call uses the
+ *     block pipeline, whose scratch covers a code buffer of up to about
+ *     357M slots (OnPair codecs; 715M for FSST-8); a selected warp-tile
+ *     variant covers about 26.8M.  Larger inputs return FP_ERR_ARG with the
+ *     limit in fp_last_error() -- use fp_decode for them.
  *   - the first call on a device looks up and clears the array
  *     (synchronously); make that first call before any stream capture.
  *   - every call, on any stream, shares the one array per device: calls

@@ -491,7 +491,11 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     if (!d_status || reinterpret_cast<uintptr_t>(d_status) % 4) return fail(FP_ERR_ARG, "d_status must be a 4-byte aligned device pointer");
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
     const uint64_t max_slots = max_slots_of(codec, codes_bytes);
-    const Variant* var = variant_get(codec, selected_variant(codec, max_slots));
+    // Unless a variant was selected, the block pipeline: its scratch (12 bytes
+    // per 4,096-slot tile) covers far larger inputs than warp tiles' (20 bytes
+    // per 512-slot tile).
+    const int sel = g_selected[codec].load();
+    const Variant* var = variant_get(codec, sel >= 0 ? sel : (codec == FP_FSST8 ? 1 : 0));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
