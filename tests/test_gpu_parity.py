@@ -30,6 +30,17 @@ def variants(fp, codec):
     return list(range(fp.variant_count(codec)))
 
 
+def each_variant(fp, codec):
+    """Select every compiled variant of the codec in turn (block pipeline and
+    warp tiles, every tile shape), then restore the defaults."""
+    try:
+        for v in variants(fp, codec):
+            fp.variant_select(codec, v)
+            yield v
+    finally:
+        fp.variant_select(codec, -1)
+
+
 @pytest.mark.parametrize("codec", CODECS)
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_generated_columns_all_variants(fp, codec, seed):
@@ -80,10 +91,11 @@ def _tokens(codec, rng, n, lo=1, hi=None):
 
 @pytest.mark.parametrize("codec", CODECS)
 def test_empty_column(fp, codec):
-    col = make_column(codec, [b"ab"], [], [0])
-    assert_same(col)
-    col = make_column(codec, [b"ab"], [], [0, 0, 0, 0])
-    assert_same(col)
+    for _ in each_variant(fp, codec):
+        col = make_column(codec, [b"ab"], [], [0])
+        assert_same(col)
+        col = make_column(codec, [b"ab"], [], [0, 0, 0, 0])
+        assert_same(col)
 
 
 @pytest.mark.parametrize("codec", CODECS)
@@ -155,7 +167,9 @@ def test_output_size_residues_mod_16(fp, codec):
             slots2 = np.concatenate([slots, np.full(extra, one)])
             col2 = make_column(codec, toks2, slots2, [0, slots2.size])
             assert oracle_decode(col2).total % 16 == r
-            assert_same(col2)
+            dc = DeviceColumn(col2)
+            for _ in each_variant(fp, codec):
+                assert_same(col2, dc)
 
 
 @pytest.mark.parametrize("codec", CODECS)
@@ -171,16 +185,17 @@ def test_slices_with_nonzero_first_offset(fp, codec, start):
     i1 = min(co.size - 1, i0 + 1500)
     sub = co[i0:i1 + 1].copy()
     t = torch.from_numpy(sub.view(np.int32)).cuda()
-    st, data, offs, guard_ok, _ = dc.decode(code_offsets=t, n_strings=sub.size - 1)
-    assert st == fp.OK and guard_ok
-    base = full.offsets[i0]
-    np.testing.assert_array_equal(offs, full.offsets[i0:i1 + 1] - base)
-    np.testing.assert_array_equal(data, full.data[base:full.offsets[i1]])
-    # a slice that starts at an arbitrary (odd) slot inside a string
-    if codec != FSST8:
-        sub2 = np.array([start, start + 17, start + 900], np.uint32)
-        col2 = synth.Column(codec, col.dictionary, col.stream, sub2, col.n_slots)
-        assert_same(col2, dc, code_offsets=torch.from_numpy(sub2.view(np.int32)).cuda(), n_strings=2)
+    for _ in each_variant(fp, codec):
+        st, data, offs, guard_ok, _ = dc.decode(code_offsets=t, n_strings=sub.size - 1)
+        assert st == fp.OK and guard_ok
+        base = full.offsets[i0]
+        np.testing.assert_array_equal(offs, full.offsets[i0:i1 + 1] - base)
+        np.testing.assert_array_equal(data, full.data[base:full.offsets[i1]])
+        # a slice that starts at an arbitrary (odd) slot inside a string
+        if codec != FSST8:
+            sub2 = np.array([start, start + 17, start + 900], np.uint32)
+            col2 = synth.Column(codec, col.dictionary, col.stream, sub2, col.n_slots)
+            assert_same(col2, dc, code_offsets=torch.from_numpy(sub2.view(np.int32)).cuda(), n_strings=2)
 
 
 def test_fsst8_escape_runs_across_tiles(fp):
@@ -215,34 +230,43 @@ def test_fsst8_escape_runs_across_tiles(fp):
     for shift in (1, 2, 15, 16, 17, 255):
         pad = [0] * shift
         col2 = make_column(FSST8, toks, pad + units, np.concatenate([[0], offs + shift]))
-        assert_same(col2)
+        dc2 = DeviceColumn(col2)
+        for _ in each_variant(fp, FSST8):
+            assert_same(col2, dc2)
 
 
 # --------------------------------------------------------------------------
 # errors: reported through fp_sync_status, writes stay in bounds
 # --------------------------------------------------------------------------
 
-def test_corrupt_code(fp):
-    col = make_column(ONPAIR16, [b"a", b"bc"], [0, 1, 5, 1] * 3000, [0, 6000, 12000])
-    st, _, _, guard_ok, _ = DeviceColumn(col).decode(capacity=40000)
-    assert st == fp.ERR_CORRUPT and guard_ok
+@pytest.mark.parametrize("codec", [ONPAIR16, ONPAIR12])
+def test_corrupt_code(fp, codec):
+    col = make_column(codec, [b"a", b"bc"], [0, 1, 5, 1] * 3000, [0, 6000, 12000])
+    dc = DeviceColumn(col)
+    for _ in each_variant(fp, codec):
+        st, _, _, guard_ok, _ = dc.decode(capacity=40000)
+        assert st == fp.ERR_CORRUPT and guard_ok
 
 
 def test_dangling_escape(fp):
     col = make_column(FSST8, [b"a", b"bc"], [0, 1, 255, 1, 0], [0, 3, 5])
-    st, _, _, guard_ok, _ = DeviceColumn(col).decode(capacity=100)
-    assert st == fp.ERR_CORRUPT and guard_ok
+    dc = DeviceColumn(col)
+    for _ in each_variant(fp, FSST8):
+        st, _, _, guard_ok, _ = dc.decode(capacity=100)
+        assert st == fp.ERR_CORRUPT and guard_ok
 
 
 @pytest.mark.parametrize("codec", CODECS)
 def test_bad_code_offsets(fp, codec):
     toks = [b"a", b"bc"]
     col = make_column(codec, toks, [0, 1] * 5000, [0, 4000, 3000, 10000])
-    st, _, _, guard_ok, _ = DeviceColumn(col).decode(capacity=30000)
-    assert st == fp.ERR_CORRUPT and guard_ok
-    col = make_column(codec, toks, [0, 1] * 50, [0, 60, 150])
-    st, _, _, guard_ok, _ = DeviceColumn(col).decode(capacity=30000)
-    assert st == fp.ERR_CORRUPT and guard_ok
+    col2 = make_column(codec, toks, [0, 1] * 50, [0, 60, 150])
+    dc, dc2 = DeviceColumn(col), DeviceColumn(col2)
+    for _ in each_variant(fp, codec):
+        st, _, _, guard_ok, _ = dc.decode(capacity=30000)
+        assert st == fp.ERR_CORRUPT and guard_ok
+        st, _, _, guard_ok, _ = dc2.decode(capacity=30000)
+        assert st == fp.ERR_CORRUPT and guard_ok
 
 
 @pytest.mark.parametrize("codec", CODECS)
@@ -250,10 +274,11 @@ def test_capacity(fp, codec):
     col = synth.column(codec, 31, 3000)
     total = oracle_decode(col).total
     dc = DeviceColumn(col)
-    for cap in (0, 1, total // 2, total - 1):
-        st, _, _, guard_ok, _ = dc.decode(capacity=cap)
-        assert st == fp.ERR_CAPACITY and guard_ok, cap
-    assert_same(col, dc, capacity=total)
+    for _ in each_variant(fp, codec):
+        for cap in (0, 1, total // 2, total - 1):
+            st, _, _, guard_ok, _ = dc.decode(capacity=cap)
+            assert st == fp.ERR_CAPACITY and guard_ok, cap
+        assert_same(col, dc, capacity=total)
 
 
 def test_argument_errors(fp):
