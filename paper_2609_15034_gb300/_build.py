@@ -40,7 +40,10 @@ def _inputs_digest() -> str:
             h.update(name.encode())
             with open(path, "rb") as f:
                 h.update(f.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    # flags without this checkout's absolute paths, so the digest names the
+    # sources and options, not where they sit
+    flags = [f.replace(INCLUDE, "<include>").replace(CSRC, "<csrc>") for f in ARCH + NVCC_FLAGS]
+    h.update(" ".join(flags).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
