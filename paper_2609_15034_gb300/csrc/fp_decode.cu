@@ -101,12 +101,13 @@ const Variant* variant_get(int codec, int v) {
 // OnPair-16 warp tiles, 8 warps per block (dictionary through L1) for large
 // buffers (790 vs 551 GB/s at 10M strings) and the one-launch block pipeline
 // for small ones (220 vs 171 GB/s at 100k strings, where the warp tiles'
-// extra launches dominate); FSST-8 block pipeline with 32 slots per thread.
+// extra launches dominate); FSST-8 warp tiles with 32 slots per lane (811 vs
+// 757 GB/s for the block pipeline at 16M strings).
 int variant_default(int codec, uint64_t max_slots) {
     switch (codec) {
         case FP_ONPAIR12: return 5;
         case FP_ONPAIR16: return max_slots >= (1ull << 23) ? 3 : 0;
-        case FP_FSST8: return 1;
+        case FP_FSST8: return 3;
         default: return 0;
     }
 }

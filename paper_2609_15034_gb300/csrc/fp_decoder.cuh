@@ -349,55 +349,61 @@ constexpr u32 FB_HI_SHIFT = 12;      // 5 bits
 
 // Per-thread assembly state: the current 16-byte output chunk c[0..3] and
 // how many of its bytes are filled (including a predecessor's bytes when the
-// thread's output starts inside the chunk).
+// thread's output starts inside the chunk).  When the thread's first chunk
+// is shared with its predecessor, that chunk is stored into the thread's
+// head slot in shared memory instead of global memory; `tgt` points at
+// wherever the current chunk goes, so each insert stores through one
+// pointer and needs no test of which chunk it completes.
 struct Assembler {
     u32 c[4];
     u32 f;          // filled bytes of the current chunk
     u32 f0;         // first byte of this thread in its first chunk
-    uint4* dst;     // current chunk in global memory
-    uint4* dst0;    // first chunk
-    bool head_open; // the first chunk is shared with the predecessor and not yet complete
-    uint4 fa, fb;
+    uint4* g;       // current chunk in global memory
+    uint4* dst0;    // first chunk in global memory
+    uint4* tgt;     // where the current chunk is stored when it completes
+    uint4* head;    // the thread's head slot (shared memory, generic address)
+    uint4 fb;
     u32 meta;
 
-    __device__ __forceinline__ void begin(uint8_t* out, u64 O) {
+    __device__ __forceinline__ void begin(uint8_t* out, u64 O, uint4* head_slot) {
         c[0] = c[1] = c[2] = c[3] = 0u;
         f0 = (u32)(O & 15u);
         f = f0;
-        dst = reinterpret_cast<uint4*>(out) + (O >> 4);
-        dst0 = dst;
-        head_open = (f0 != 0u);
+        g = reinterpret_cast<uint4*>(out) + (O >> 4);
+        dst0 = g;
+        head = head_slot;
+        tgt = f0 != 0u ? head_slot : g;
         meta = 0u;
-        fa = make_uint4(0, 0, 0, 0);
         fb = make_uint4(0, 0, 0, 0);
     }
     // Append a token (zero padded beyond len).  When the chunk completes it is
-    // stored (or kept as the lead fragment) and the token's overflow starts
-    // the next chunk.  No branches: every step runs the same instructions.
+    // stored and the token's overflow starts the next chunk.  No branches:
+    // every step runs the same instructions.
     __device__ __forceinline__ void put(uint4 t, u32 len) {
         u32 s[8];
         shift_token(t, f, s);
-        c[0] |= s[0]; c[1] |= s[1]; c[2] |= s[2]; c[3] |= s[3];
         f += len;
         const bool fl = f >= 16u;
-        const uint4 full = make_uint4(c[0], c[1], c[2], c[3]);
-        if (fl && !head_open) __stcs(dst, full);
-        if (fl && head_open) fa = full;
-        head_open = head_open && !fl;
-        c[0] = fl ? s[4] : c[0];
-        c[1] = fl ? s[5] : c[1];
-        c[2] = fl ? s[6] : c[2];
-        c[3] = fl ? s[7] : c[3];
-        f = fl ? f - 16u : f;
-        dst += fl ? 1 : 0;
+        const uint4 full = make_uint4(c[0] | s[0], c[1] | s[1], c[2] | s[2], c[3] | s[3]);
+        if (fl) *tgt = full;
+        g += fl ? 1 : 0;
+        tgt = fl ? g : tgt;
+        c[0] = fl ? s[4] : full.x;
+        c[1] = fl ? s[5] : full.y;
+        c[2] = fl ? s[6] : full.z;
+        c[3] = fl ? s[7] : full.w;
+        f &= 15u;   // below 16 before the insert, below 32 after it
     }
     // Close the thread's range; `nonempty` = it produced at least one byte.
+    // Afterwards the head slot holds the thread's lead fragment (FA_VALID).
     __device__ __forceinline__ void finish(bool nonempty) {
         if (!nonempty) return;
-        if (f0 != 0u && !head_open) meta |= FA_VALID | (f0 << FA_LO_SHIFT) | (16u << FA_HI_SHIFT);
+        const bool head_shared = f0 != 0u;
+        const bool head_open = head_shared && tgt == head;   // the first chunk never completed
+        if (head_shared && !head_open) meta |= FA_VALID | (f0 << FA_LO_SHIFT) | (16u << FA_HI_SHIFT);
         if (head_open) {
             if (f > f0) {
-                fa = make_uint4(c[0], c[1], c[2], c[3]);
+                *head = make_uint4(c[0], c[1], c[2], c[3]);
                 meta |= FA_VALID | (f0 << FA_LO_SHIFT) | (f << FA_HI_SHIFT);
             }
         } else if (f > 0u) {
@@ -1013,7 +1019,7 @@ struct Decoder {
 
         const bool skip = p.size_only || tile_incl > p.capacity;
         Assembler as;
-        as.begin(p.out, tile_excl + thr);
+        as.begin(p.out, tile_excl + thr, &sm.fa[wtid]);
         u32 produced = 0;
         if (!FSST) {
 #pragma unroll
@@ -1084,18 +1090,16 @@ struct Decoder {
         }
         sm.thr_excl[wtid] = thr;
         as.finish(produced > 0u && !skip);
-        sm.fa[wtid] = as.fa;
-        sm.fb[wtid] = as.fb;
         sm.meta[wtid] = as.meta;
         bar_sync(kBarWork, kWork);
 
         // merge chunks shared between threads
         if (!skip && produced > 0u) {
             if (as.meta & FB_VALID)
-                combine_and_store(as.dst, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)wtid + 1, sm.fa, sm.meta);
+                combine_and_store(as.g, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)wtid + 1, sm.fa, sm.meta);
             if ((as.meta & FA_VALID) && thr == 0u)
-                combine_and_store(as.dst0, as.fa, (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
-                                  (int)wtid + 1, sm.fa, sm.meta);
+                combine_and_store(as.dst0, sm.fa[wtid], (as.meta >> FA_LO_SHIFT) & 31u,
+                                  (as.meta >> FA_HI_SHIFT) & 31u, (int)wtid + 1, sm.fa, sm.meta);
         }
 
         // string offsets of the boundaries the tile owns

@@ -403,7 +403,7 @@ struct WarpCore {
         const bool skip = p.size_only || tile_incl > p.capacity;
 
         Assembler as;
-        as.begin(p.out, tile_excl + thr);
+        as.begin(p.out, tile_excl + thr, &area.fa[lane]);
         u32 produced = 0;
         if (!FSST) {
 #pragma unroll
@@ -473,8 +473,6 @@ struct WarpCore {
         }
         area.thr_excl[lane] = thr;
         as.finish(produced > 0u && !skip);
-        area.fa[lane] = as.fa;
-        area.fb[lane] = as.fb;
         area.meta[lane] = as.meta;
         __syncwarp();
 
@@ -484,11 +482,11 @@ struct WarpCore {
         Partial pd;
         pd.pending = false;
         if (wrote && (as.meta & FB_VALID))
-            combine_lanes(as.dst, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
+            combine_lanes(as.g, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
         store_partials(pd);
         pd.pending = false;
         if (wrote && (as.meta & FA_VALID) && thr == 0u)
-            combine_lanes(as.dst0, as.fa, (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
+            combine_lanes(as.dst0, area.fa[lane], (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
                           (int)lane + 1, area.fa, area.meta, pd);
         store_partials(pd);
 
