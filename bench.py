@@ -400,7 +400,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": load_traffic(args.workload), "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": round(avg_launch_s * 1e3, 4)},
         "clocks": clocks,
-        "gpu_launches": vinfo["launches_per_call"] * args.steps,   # index pass [+ reduce + tile scan] + decode
+        "gpu_launches": vinfo["launches_per_call"] * args.steps,   # index pass (+ reduce in the same launch, tile scan) + decode
     }
     line.update(extra)
     if "e2e" not in line:

@@ -405,8 +405,9 @@ fp_status fp_serve_destroy(fp_server* server);
  * fp_variant_info   describe variant v: threads per block, slots per thread,
  *                   1 if the dictionary is staged in shared memory, and the
  *                   kernel launches of one fp_decode call (2: index pass and
- *                   block-pipeline decode; 4: index pass, reduce, tile scan
- *                   and warp-tile decode).  Any out pointer may be NULL.
+ *                   block-pipeline decode; 3: index pass and reduce in one
+ *                   launch, tile scan, warp-tile decode).  Any out pointer
+ *                   may be NULL.
  * fp_variant_select make variant v the one fp_decode uses for the codec in
  *                   this process (v = -1 restores the built-in defaults,
  *                   which depend on the size of the code buffer).

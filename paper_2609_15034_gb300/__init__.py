@@ -239,7 +239,7 @@ def variant_info(codec: int, v: int) -> dict:
     _check(lib().fp_variant_info(codec, v, ctypes.byref(t), ctypes.byref(k), ctypes.byref(s), ctypes.byref(n)),
            "fp_variant_info")
     return {"threads": t.value, "slots_per_thread": k.value, "dict_in_smem": bool(s.value),
-            "warp_tiles": n.value == 4, "launches_per_call": n.value}
+            "warp_tiles": n.value == 3, "launches_per_call": n.value}
 
 
 def variant_select(codec: int, v: int) -> None:

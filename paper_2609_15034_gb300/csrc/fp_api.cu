@@ -409,7 +409,7 @@ fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* sl
     if (threads) *threads = (uint32_t)var->threads;
     if (slots_per_thread) *slots_per_thread = (uint32_t)var->slots_per_thread;
     if (dict_in_smem) *dict_in_smem = (uint32_t)var->dict_smem;
-    if (launches_per_call) *launches_per_call = var->warp_tiles ? 4u : 2u;
+    if (launches_per_call) *launches_per_call = var->warp_tiles ? 3u : 2u;
     return FP_OK;
 }
 

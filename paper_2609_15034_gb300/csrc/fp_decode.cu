@@ -165,14 +165,16 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
     const uint64_t nb = (uint64_t)p.n_strings + 1;
     uint64_t ib = (nb + 256 * kIdxGroup - 1) / (256 * kIdxGroup);
     if (ib > (uint64_t)sms * 8) ib = (uint64_t)sms * 8;
-    index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first,
-                                                   var.warp_tiles ? reinterpret_cast<Extent*>(base + L.o_extent) : nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     void* args[] = {(void*)&p};
-    if (!var.warp_tiles) return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
+    if (!var.warp_tiles) {
+        index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first, nullptr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
+    }
 
-    // warp tiles: reduce, tile scan, decode (the index pass stored the extent)
+    // warp tiles: index pass + reduce in one launch, tile scan, decode
     Extent* xp = reinterpret_cast<Extent*>(base + L.o_extent);
     u64* agg = reinterpret_cast<u64*>(base + L.o_agg);
     u64* ex = reinterpret_cast<u64*>(base + L.o_ex);
@@ -181,8 +183,9 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
     const uint64_t rg_cap = (uint64_t)sms * 8;
     if (rg > rg_cap) rg = rg_cap;
     const Extent* cxp = xp;
-    void* rargs[] = {(void*)&p, (void*)&cxp, (void*)&agg};
-    e = cudaLaunchKernel(var.reduce, dim3((unsigned)rg), dim3(256), rargs, 0, stream);
+    u32 ib32 = (u32)ib;
+    void* rargs[] = {(void*)&p, (void*)&xp, (void*)&agg, (void*)&ib32};
+    e = cudaLaunchKernel(var.reduce, dim3((unsigned)(rg + ib)), dim3(256), rargs, 0, stream);
     if (e != cudaSuccess) return e;
     uint64_t sg = n_wt_max / kScanTile + 1;
     if (sg > (uint64_t)sms * 2) sg = (uint64_t)sms * 2;

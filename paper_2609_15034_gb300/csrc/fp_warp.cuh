@@ -536,23 +536,35 @@ struct WarpCore {
 // ---------------------------------------------------------------------------
 // Pass 1: warp-tile elements.
 // ---------------------------------------------------------------------------
+// Blocks [0, index_blocks) run the index pass (first string of every warp
+// tile; block 0 also stores the column's extent for the later passes), the
+// others the reduce: the two overlap in one launch.
 template <int CODEC, int K, bool DSMEM>
-__global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, const Extent* xp, u64* agg) {
+__global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Extent* xp, u64* agg, u32 index_blocks) {
     typedef WarpCore<CODEC, K, DSMEM> C;
     __shared__ __align__(16) uint8_t s_lens[DSMEM ? C::LENS_BYTES : 16];
+    if (blockIdx.x < index_blocks) {
+        const Extent x = column_extent(p, C::TILE);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
+        index_groups(p, x, (u32)(__ffs(C::TILE) - 1), 0, (u64)p.n_strings + 1,
+                     (u64)blockIdx.x * blockDim.x + threadIdx.x, (u64)index_blocks * blockDim.x,
+                     const_cast<u32*>(p.first));
+        return;
+    }
     if (DSMEM) {
         const uint4* src = reinterpret_cast<const uint4*>(p.dict.lens);
         for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += blockDim.x) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(src + i);
         __syncthreads();
     }
-    const Extent x = *xp;
+    const Extent x = column_extent(p, C::TILE);
     const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
     const u32 lane = threadIdx.x & 31u;
-    const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
+    const u32 rblock = blockIdx.x - index_blocks;
+    const u64 warps = (u64)(gridDim.x - index_blocks) * (blockDim.x / 32);
     u32 err = 0;
     // rounds of U tiles; the next round's loads are in flight while this one computes
     constexpr int U = 2;
-    u64 t0 = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    u64 t0 = (u64)rblock * (blockDim.x / 32) + (threadIdx.x >> 5);
     u32 wv[U][C::LANE_BYTES / 4];
     bool fast[U];
 #pragma unroll
