@@ -96,18 +96,19 @@ const Variant* variant_get(int codec, int v) {
     return (t && v >= 0 && v < n) ? &t[v] : nullptr;
 }
 
-// Defaults chosen by measurement on GB300 (synthetic columns):
-// OnPair-12 warp tiles, 10 warps per block, dictionary in shared memory;
-// OnPair-16 warp tiles, 8 warps per block (dictionary through L1) for large
-// buffers (790 vs 551 GB/s at 10M strings) and the one-launch block pipeline
-// for small ones (220 vs 171 GB/s at 100k strings, where the warp tiles'
-// extra launches dominate); FSST-8 warp tiles with 32 slots per lane (811 vs
-// 757 GB/s for the block pipeline at 16M strings).
+// Defaults chosen by measurement on GB300 (synthetic columns, every variant
+// timed at 3k..3M strings and at the full workloads): warp tiles for all three
+// codecs.  OnPair-12: dictionary staged in shared memory with 10 warps per
+// block from 2^24 slots on (1321 GB/s at 10M strings), through L1 below that
+// (637 vs 613 GB/s at 300k strings).  OnPair-16: dictionary through L1, 8
+// warps (1017 vs 817 GB/s for the block pipeline at 3M strings, 470 vs 409 at
+// 300k).  FSST-8: 32 slots per lane from 2^22 slots on (812 vs 769 GB/s at 3M
+// strings), 16 below.
 int variant_default(int codec, uint64_t max_slots) {
     switch (codec) {
-        case FP_ONPAIR12: return 5;
-        case FP_ONPAIR16: return max_slots >= (1ull << 23) ? 3 : 0;
-        case FP_FSST8: return 3;
+        case FP_ONPAIR12: return max_slots >= (1ull << 24) ? 5 : 4;
+        case FP_ONPAIR16: return 3;
+        case FP_FSST8: return max_slots >= (1ull << 22) ? 3 : 2;
         default: return 0;
     }
 }
