@@ -54,3 +54,47 @@ def test_product_package_does_not_import_the_oracle():
                     src = f.read()
                 assert "import oracle" not in src and "from oracle" not in src, fn
                 assert "fp_oracle" not in src, fn
+
+
+def test_variant_tables_and_size_defaults():
+    """Host logic of the decoder shapes: every compiled variant describes
+    itself consistently, the default for any code-buffer size is a valid
+    variant, a selection overrides it for every size and -1 restores it."""
+    import paper_2609_15034_gb300 as fp
+    for codec in (fp.ONPAIR16, fp.ONPAIR12, fp.FSST8):
+        n = fp.variant_count(codec)
+        assert n >= 2
+        for v in range(n):
+            info = fp.variant_info(codec, v)
+            assert info["threads"] % 32 == 0 and 32 <= info["threads"] <= 1024
+            assert info["slots_per_thread"] in (8, 16, 32)
+            assert info["launches_per_call"] in (2, 3)
+            if codec == fp.ONPAIR16:
+                assert not info["dict_in_smem"]   # a 1 MiB table does not fit
+        sizes = [0, 1, 16, 1 << 20, (1 << 22) - 1, 1 << 22, 1 << 24, 1 << 26, 1 << 30, 1 << 34]
+        defaults = [fp.variant_for(codec, b) for b in sizes]
+        assert all(0 <= d < n for d in defaults)
+        # large columns use warp tiles
+        assert fp.variant_info(codec, fp.variant_for(codec, 1 << 34))["launches_per_call"] == 3
+        for v in range(n):
+            fp.variant_select(codec, v)
+            assert all(fp.variant_for(codec, b) == v for b in sizes)
+            assert fp.variant_selected(codec) == v
+        fp.variant_select(codec, -1)
+        assert [fp.variant_for(codec, b) for b in sizes] == defaults
+    with pytest.raises(fp.FastPairError):
+        fp.variant_info(fp.ONPAIR12, fp.variant_count(fp.ONPAIR12))
+    assert fp.variant_for(9, 1 << 20) == -1
+
+
+def test_batch_configuration_table():
+    import paper_2609_15034_gb300 as fp
+    n = fp.batch_config_count()
+    assert n >= 2
+    for c in range(n):
+        info = fp.batch_config_info(c)
+        assert len(info["slots_per_thread"]) == 3
+        assert all(k in (8, 16, 32) for k in info["slots_per_thread"])
+        assert info["blocks_per_sm"] >= 1
+    with pytest.raises(fp.FastPairError):
+        fp.batch_config_info(n)
