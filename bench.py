@@ -52,7 +52,7 @@ SERVE_WORKLOADS = {
 }
 METRIC = "decoded GB/s (single-column decode, inputs resident in HBM)"
 SERVE_METRIC = "served decode: aggregate decoded GB/s at the offered load, with p50/p99 latency"
-SERVE_DEFAULT_CONFIG = 3   # the library's default batch configuration (warp tiles)
+SERVE_DEFAULT_CONFIG = 4   # the library's default batch configuration (warp tiles, one block of 16 warps per SM)
 BATCH_METRIC = "decoded GB/s (batched decode of many chunks, inputs resident in HBM)"
 L2_BYTES = 126 * 1024 * 1024
 

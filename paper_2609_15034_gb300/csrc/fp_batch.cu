@@ -268,6 +268,7 @@ const std::vector<BatchKernel>& batch_kernels() {
         make_batch_kernel<16, 16, 16, 2>(),
         make_batch_kernel<8, 8, 16, 2>(),
         make_wbatch_kernel<16, 16, 32, 8, 2>(),
+        make_wbatch_kernel<16, 16, 32, 16, 1>(),
     };
     return v;
 }
@@ -278,7 +279,7 @@ struct Config {
     int bps;      // blocks per SM launched (<= what fits)
 };
 const std::vector<Config>& configs() {
-    static const std::vector<Config> v = {{0, 2}, {0, 1}, {1, 2}, {2, 2}};
+    static const std::vector<Config> v = {{0, 2}, {0, 1}, {1, 2}, {2, 2}, {3, 1}};
     return v;
 }
 
@@ -731,10 +732,10 @@ fp_status plan_create(const fp_chunk* chunks, uint32_t n, int force_cfg, const c
 
 namespace fp {
 
-// Warp tiles (16/16/32 slots per lane, 2 blocks of 8 warps per SM): the
-// fastest configuration on the mixed 4,096-chunk batch (49 ms vs 60 ms for
-// the block pipeline).
-int batch_config_default() { return 3; }
+// Warp tiles (16/16/32 slots per lane, one block of 16 warps per SM): the
+// fastest configuration on the mixed 4,096-chunk batch (41 ms, against 50 ms
+// for two blocks of 8 warps and 55 ms for the block pipeline).
+int batch_config_default() { return 4; }
 
 fp_status wave_init(WaveBuffers& W, uint32_t cap_chunks) {
     int dev = 0;

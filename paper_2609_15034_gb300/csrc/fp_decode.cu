@@ -61,6 +61,7 @@ static const Variant* table_for(int codec, int* n) {
         make_variant<FP_ONPAIR16, 8, false, 2>(),
         make_warp_variant<FP_ONPAIR16, 16, false, 8, 3>(),
         make_warp_variant<FP_ONPAIR16, 16, false, 8, 2>(),
+        make_warp_variant<FP_ONPAIR16, 16, false, 16, 1>(),
     };
     static const Variant v12[] = {
         make_variant<FP_ONPAIR12, 16, true, 2>(),
@@ -69,12 +70,15 @@ static const Variant* table_for(int codec, int* n) {
         make_warp_variant<FP_ONPAIR12, 16, true, 8, 2>(),
         make_warp_variant<FP_ONPAIR12, 16, false, 8, 3>(),
         make_warp_variant<FP_ONPAIR12, 16, true, 10, 2>(),
+        make_warp_variant<FP_ONPAIR12, 16, true, 16, 1>(),
+        make_warp_variant<FP_ONPAIR12, 16, false, 20, 1>(),
     };
     static const Variant v8[] = {
         make_variant<FP_FSST8, 16, true, 2>(),
         make_variant<FP_FSST8, 32, true, 2>(),
         make_warp_variant<FP_FSST8, 16, true, 8, 3>(),
         make_warp_variant<FP_FSST8, 32, true, 8, 2>(),
+        make_warp_variant<FP_FSST8, 32, true, 16, 1>(),
     };
     switch (codec) {
         case FP_ONPAIR16: *n = (int)(sizeof(v16) / sizeof(v16[0])); return v16;
@@ -97,18 +101,20 @@ const Variant* variant_get(int codec, int v) {
 }
 
 // Defaults chosen by measurement on GB300 (synthetic columns, every variant
-// timed at 3k..3M strings and at the full workloads): warp tiles for all three
-// codecs.  OnPair-12: dictionary staged in shared memory with 10 warps per
-// block from 2^24 slots on (1321 GB/s at 10M strings), through L1 below that
-// (637 vs 613 GB/s at 300k strings).  OnPair-16: dictionary through L1, 8
-// warps (1017 vs 817 GB/s for the block pipeline at 3M strings, 470 vs 409 at
-// 300k).  FSST-8: 32 slots per lane from 2^22 slots on (812 vs 769 GB/s at 3M
-// strings), 16 below.
+// timed at 30k..10M strings): warp tiles for all three codecs, one block of
+// 16 warps per SM for large columns.  The one-block shapes run the same code
+// with the same registers and warps per SM as two blocks of 8 warps, with one
+// copy of the dictionary per SM instead of two; they were faster for every
+// codec (10M strings: OnPair-12 1446 vs 1342
+// GB/s, FSST-8 963 vs 902, OnPair-16 1029 vs 990).  OnPair-12 below 2^23
+// slots reads the dictionary through L1 (20 warps; staging it per block does
+// not pay: 637 vs 613 GB/s at 300k strings); FSST-8 below 2^22 slots uses
+// 16-slot lanes.
 int variant_default(int codec, uint64_t max_slots) {
     switch (codec) {
-        case FP_ONPAIR12: return max_slots >= (1ull << 24) ? 5 : 4;
-        case FP_ONPAIR16: return 3;
-        case FP_FSST8: return max_slots >= (1ull << 22) ? 3 : 2;
+        case FP_ONPAIR12: return max_slots >= (1ull << 23) ? 6 : 7;
+        case FP_ONPAIR16: return 4;
+        case FP_FSST8: return max_slots >= (1ull << 22) ? 4 : 2;
         default: return 0;
     }
 }
