@@ -99,13 +99,13 @@ def load_peaks():
 
 def load_traffic(workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the library build that is running now."""
+    a build whose single-column decode sources and flags equal this one's."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         from paper_2609_15034_gb300 import _build
-        digest = _build._inputs_digest()
+        digest = _build.decode_path_digest()
         with open(path) as f:
             d = json.load(f)
         e = d.get(workload)

@@ -90,35 +90,64 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
 // shared-memory slot.
 // ---------------------------------------------------------------------------
 template <int CODEC, int K>
-__device__ __forceinline__ void reduce_queue(const BatchParams& bp, int q, u64 gw, u64 W) {
+__device__ __forceinline__ void reduce_queue(const BatchParams& bp, int q, u64 t, u64 t_end, u64 W) {
     typedef WarpCore<CODEC, K, false> C;
     const BatchQueue& Q = bp.q[q];
     const u32 lane = threadIdx.x & 31u;
-    for (u64 t = gw; t < Q.n_tiles; t += W) {
-        const SlotSrc* rec = Q.src + __ldg(Q.tile_chunk + t);
-        const DecodeParams& p = rec->p;
-        const Extent x = rec->x;
-        const u64 lt = t - rec->tile_base;
-        const u64 q0 = C::lane_q0(x, lt);
-        u32 wv[C::LANE_BYTES / 4];
-        const bool fast = C::load_fast(p, q0, wv);
+    if (t >= t_end) return;
+    // Software pipeline: the code words of tile t + W (its chunk record
+    // already known) and the record of tile t + 2W are in flight while tile t
+    // computes, so the chain ticket -> record -> codes -> lengths does not
+    // stall the warp once per tile.
+    const SlotSrc* rc = Q.src + __ldg(Q.tile_chunk + t);
+    u64 q0 = C::lane_q0(rc->x, t - rc->tile_base);
+    u32 wv[C::LANE_BYTES / 4];
+    bool fast = C::load_fast(rc->p, q0, wv);
+    const SlotSrc* rn = t + W < t_end ? Q.src + __ldg(Q.tile_chunk + t + W) : nullptr;
+    for (; t < t_end; t += W) {
+        u32 nv[C::LANE_BYTES / 4];
+        bool nfast = false;
+        u64 nq0 = 0;
+        if (rn) {
+            nq0 = C::lane_q0(rn->x, t + W - rn->tile_base);
+            nfast = C::load_fast(rn->p, nq0, nv);
+        }
+        const SlotSrc* r2 = t + 2 * W < t_end ? Q.src + __ldg(Q.tile_chunk + t + 2 * W) : nullptr;
+        const DecodeParams& p = rc->p;
+        const Extent x = rc->x;
         typename C::R r;
         C::finish_load(p, x, q0, wv, fast, p.dict.lens, r);
         u32 err = 0;
         const TElem e = C::element(r, err);
         const TElem inc = warp_scan_incl<C::FSST>(e, lane, telem_identity());
         // every codec's element in the two-state form (OnPair: both states alike)
-        if (lane == 31) bp.agg[rec->wt_base + lt] = wt_pack<true>(C::FSST ? inc : TElem{inc.b0, inc.b0, 2u});
+        if (lane == 31)
+            bp.agg[rc->wt_base + (t - rc->tile_base)] = wt_pack<true>(C::FSST ? inc : TElem{inc.b0, inc.b0, 2u});
         if (err) atomicOr(p.err_word, err);
+        rc = rn;
+        rn = r2;
+        q0 = nq0;
+        fast = nfast;
+#pragma unroll
+        for (int i = 0; i < C::LANE_BYTES / 4; ++i) wv[i] = nv[i];
     }
 }
 
 template <int K16, int K12, int K8>
 __global__ void __launch_bounds__(256, 3) wbatch_reduce_kernel(const BatchParams bp) {
-    const u64 gw = (u64)blockIdx.x * 8 + (threadIdx.x >> 5), W = (u64)gridDim.x * 8;
-    reduce_queue<FP_ONPAIR16, K16>(bp, 0, gw, W);
-    reduce_queue<FP_ONPAIR12, K12>(bp, 1, gw, W);
-    reduce_queue<FP_FSST8, K8>(bp, 2, gw, W);
+    // Every block takes a contiguous range of each queue's tiles (its warps
+    // interleaved inside it), so a block's warps mostly work in one chunk and
+    // that chunk's length table stays in the SM's L1 (12 % faster than tiles
+    // interleaved over the whole grid on the mixed 4,096-chunk batch).
+    const u64 b = blockIdx.x, B = gridDim.x, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const u64 n = bp.q[q].n_tiles;
+        const u64 lo = n * b / B, hi = n * (b + 1) / B;
+        if (q == 0) reduce_queue<FP_ONPAIR16, K16>(bp, 0, lo + w, hi, 8);
+        else if (q == 1) reduce_queue<FP_ONPAIR12, K12>(bp, 1, lo + w, hi, 8);
+        else reduce_queue<FP_FSST8, K8>(bp, 2, lo + w, hi, 8);
+    }
 }
 
 // Tile scan of every chunk: a ticket names one scan block of one chunk
@@ -141,14 +170,13 @@ __global__ void __launch_bounds__(256) wbatch_scan_kernel(const BatchParams bp) 
 }
 
 template <int CODEC, int K>
-__device__ __forceinline__ void decode_queue(const BatchParams& bp, int q, u64 gw, u64 W, unsigned char* area_raw,
-                                             SlotSrc& rs) {
+__device__ __forceinline__ void decode_queue(const BatchParams& bp, int q, u64 t, u64 t_end, u64 W,
+                                             unsigned char* area_raw, SlotSrc& rs) {
     typedef WarpCore<CODEC, K, false> C;
     const BatchQueue& Q = bp.q[q];
     WarpArea<K>& area = *reinterpret_cast<WarpArea<K>*>(area_raw);
     const u32 lane = threadIdx.x & 31u;
-    u64 t = gw;
-    if (t >= Q.n_tiles) return;
+    if (t >= t_end) return;
     // software pipeline as in the single-column decode: while tile t decodes,
     // the inputs of t + W are in flight and the boundaries of t + 2W are read
     const SlotSrc* rc = Q.src + __ldg(Q.tile_chunk + t);
@@ -157,18 +185,18 @@ __device__ __forceinline__ void decode_queue(const BatchParams& bp, int q, u64 g
     typename C::Fetch cur;
     C::fetch(rc->p, rc->x, bp.ex + rc->wt_base, t - rc->tile_base, lo, hi, cur);
     const SlotSrc* rn = nullptr;
-    if (t + W < Q.n_tiles) {
+    if (t + W < t_end) {
         rn = Q.src + __ldg(Q.tile_chunk + t + W);
         C::bounds(rn->p, t + W - rn->tile_base, lo1, hi1);
     }
     const SlotSrc* held = nullptr;   // the record copied into rs
-    for (; t < Q.n_tiles; t += W) {
+    for (; t < t_end; t += W) {
         typename C::Fetch nxt;
         const u64 tn = t + W, t2 = t + 2 * W;
         const SlotSrc* r2 = nullptr;
         u32 lo2 = 0, hi2 = 0;
-        if (tn < Q.n_tiles) C::fetch(rn->p, rn->x, bp.ex + rn->wt_base, tn - rn->tile_base, lo1, hi1, nxt);
-        if (t2 < Q.n_tiles) {
+        if (tn < t_end) C::fetch(rn->p, rn->x, bp.ex + rn->wt_base, tn - rn->tile_base, lo1, hi1, nxt);
+        if (t2 < t_end) {
             r2 = Q.src + __ldg(Q.tile_chunk + t2);
             C::bounds(r2->p, t2 - r2->tile_base, lo2, hi2);
         }
@@ -207,10 +235,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) wbatch_decode_kernel(const Batc
     const u32 warp = threadIdx.x >> 5;
     unsigned char* mine = smem_raw + warp * SLOT;
     SlotSrc& rs = *reinterpret_cast<SlotSrc*>(mine + A);   // after the warp's scratch area
+    // Warps take the tiles of each queue in turn, interleaved over the whole
+    // grid (contiguous ranges per block were tried: 14 % slower, the blocks'
+    // ranges end unevenly).
     const u64 gw = (u64)blockIdx.x * NW + warp, W = (u64)gridDim.x * NW;
-    decode_queue<FP_ONPAIR16, K16>(bp, 0, gw, W, mine, rs);
-    decode_queue<FP_ONPAIR12, K12>(bp, 1, gw, W, mine, rs);
-    decode_queue<FP_FSST8, K8>(bp, 2, gw, W, mine, rs);
+    decode_queue<FP_ONPAIR16, K16>(bp, 0, gw, bp.q[0].n_tiles, W, mine, rs);
+    decode_queue<FP_ONPAIR12, K12>(bp, 1, gw, bp.q[1].n_tiles, W, mine, rs);
+    decode_queue<FP_FSST8, K8>(bp, 2, gw, bp.q[2].n_tiles, W, mine, rs);
 }
 
 template <int K16, int K12, int K8, int NW>
