@@ -587,8 +587,14 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
                 typename C::R r;
                 C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r);
                 const TElem e = C::element(r, err);
-                const TElem inc = warp_scan_incl<C::FSST>(e, lane, telem_identity());
-                if (lane == 31) agg[t] = wt_pack<C::FSST>(inc);
+                if (C::FSST) {
+                    const TElem inc = warp_scan_incl<true>(e, lane, telem_identity());
+                    if (lane == 31) agg[t] = wt_pack<true>(inc);
+                } else {
+                    // OnPair: the tile's element is its byte count, a plain warp sum
+                    const u32 sum = __reduce_add_sync(0xffffffffu, e.b0);
+                    if (lane == 31) agg[t] = sum;
+                }
             }
         }
 #pragma unroll
