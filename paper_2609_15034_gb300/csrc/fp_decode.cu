@@ -1,18 +1,18 @@
-// Single-column decoder for sm_103a: the kernel instantiations of the
-// decode pipeline (fp_decoder.cuh), its variant table and the launch of the
-// index pass plus the decode kernel.
+// Single-column decoder for sm_103a: the kernel instantiations of the block
+// pipeline (fp_decoder.cuh) and of the warp-tile decoder (fp_warp.cuh), the
+// variant table with its size-dependent defaults, and the launches of one
+// decode call (index pass + block-pipeline decode, or index pass and reduce
+// in one grid + tile scan + warp-tile decode).
 #include "fp_decoder.cuh"
 #include "fp_warp.cuh"
 
 namespace fp {
 namespace {
 
-// Index pass over one column (grid-stride over its string boundaries);
-// block 0 also stores the column's extent for the later passes (xp may be
-// null).
-__global__ void __launch_bounds__(256) index_kernel(const DecodeParams p, u32 tile, u32* first, Extent* xp) {
+// Index pass of the block pipeline over one column (grid-stride over its
+// string boundaries).
+__global__ void __launch_bounds__(256) index_kernel(const DecodeParams p, u32 tile, u32* first) {
     const Extent x = column_extent(p, tile);
-    if (xp && blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
     index_groups(p, x, (u32)(__ffsll((long long)tile) - 1), 0, (u64)p.n_strings + 1,
                  (u64)blockIdx.x * blockDim.x + threadIdx.x, (u64)gridDim.x * blockDim.x, first);
 }
@@ -175,7 +175,7 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
     cudaError_t e;
     void* args[] = {(void*)&p};
     if (!var.warp_tiles) {
-        index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first, nullptr);
+        index_kernel<<<(unsigned)ib, 256, 0, stream>>>(p, (u32)tile, first);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);

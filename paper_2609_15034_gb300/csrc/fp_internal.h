@@ -116,8 +116,8 @@ struct Variant {
     size_t smem_bytes;
     const void* kernel;   // the decode kernel
     int warp_tiles;       // 0: block pipeline (one launch after the index pass);
-                          // 1: warp tiles (reduce, tile scan and warp decode launches)
-    const void* reduce;   // warp tiles: the reduce kernel
+                          // 1: warp tiles (index pass + reduce, tile scan and warp decode launches)
+    const void* reduce;   // warp tiles: the reduce kernel (its first blocks run the index pass)
     const void* scan;     // warp tiles: the tile scan kernel
 };
 
@@ -160,7 +160,7 @@ struct WaveBuffers {
 fp_status wave_init(WaveBuffers& W, uint32_t cap_chunks);
 void wave_free(WaveBuffers& W);
 // Enqueue the decode of `n` chunks on `stream`: upload the tables, clear
-// the per-chunk words, index pass + persistent decode, then copy the
+// the per-chunk words, run the configuration's launches, then copy the
 // per-chunk results into W.h_status / W.h_total.  The previous wave of W
 // must have completed (its staging is reused).
 fp_status wave_launch(WaveBuffers& W, const fp_chunk* chunks, uint32_t n, int config, cudaStream_t stream);

@@ -1,10 +1,12 @@
 // Warp-tile decoder: the column is cut into warp tiles of 32*K code slots,
-// and a decode runs in three passes after the index pass:
+// and a decode runs in three launches:
 //
-//   reduce_kernel   each warp computes the scan element of a warp tile
-//                   (its decoded bytes; for FSST-8 the two-state element of
-//                   the escape parity) and stores it: fully parallel, the
-//                   code stream is read once;
+//   reduce_kernel   its first blocks run the index pass (the first string
+//                   boundary of every warp tile); in the others each warp
+//                   computes the scan element of a warp tile (its decoded
+//                   bytes; for FSST-8 the two-state element of the escape
+//                   parity) and stores it: fully parallel, the code stream
+//                   is read once;
 //   tiles_scan_kernel  single-pass exclusive scan of the warp-tile elements
 //                   (blocks of 2,048 elements, decoupled look-back across
 //                   blocks): every warp tile's output offset and entering
