@@ -214,8 +214,11 @@ __device__ __forceinline__ void decode_queue(const BatchParams& bp, int q, u64 t
             held = rc;
         }
         u32 err = 0;
+        // the error word's address is read before the tile: once the tile's
+        // last __syncwarp() has passed, other lanes may overwrite the record
+        unsigned* const err_word = rs.p.err_word;
         C::decode_tile(rs.p, rs.x, t - rs.tile_base, cur, nullptr, rs.p.dict.lens, area, err);
-        if (err) atomicOr(rs.p.err_word, err);
+        if (err) atomicOr(err_word, err);
         cur = nxt;
         rc = rn;
         rn = r2;

@@ -332,6 +332,29 @@ struct WarpCore {
         }
     }
 
+    // FSST-8 slots: a literal's byte, else the symbol; cw holds each slot's
+    // byte count.  In a lane whose slots are all inside the column a slot
+    // that yields no byte is an escape or a corrupt code, whose table entries
+    // (255, and those past the dictionary) are all zero, so only literals
+    // need a select there.
+    template <bool ALLV>
+    static __device__ __forceinline__ void assemble_fsst(const DecodeParams& p, const uint4* dict, const R& r,
+                                                         const u32 (&cw)[K / 4], u32 lit, Assembler& as) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const u32 bt = code_at<CODEC, K>(r, k);
+            const u32 a = (cw[k >> 2] >> ((k & 3) * 8)) & 0xffu;
+            const bool is_lit = (lit >> k) & 1u;
+            uint2 d;
+            if (DSMEM) d = reinterpret_cast<const uint2*>(dict)[bt];
+            else d = __ldg(reinterpret_cast<const uint2*>(p.dict.table) + bt);
+            uint4 tok;
+            if (ALLV) tok = make_uint4(is_lit ? bt : d.x, is_lit ? 0u : d.y, 0u, 0u);
+            else tok = make_uint4(a == 0u ? 0u : (is_lit ? bt : d.x), (a == 0u || is_lit) ? 0u : d.y, 0u, 0u);
+            as.put(tok, a);
+        }
+    }
+
     static __device__ __forceinline__ u64 lane_q0(const Extent& x, u64 t) {
         return (x.first_tile + t) * (u64)TILE + (u64)(threadIdx.x & 31u) * K;
     }
@@ -459,18 +482,8 @@ struct WarpCore {
             for (int j = 0; j < K / 4; ++j) area.contrib[j][lane] = cw[j];
             area.lit_mask[lane] = lit;
             if (!skip) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const u32 bt = code_at<CODEC, K>(r, k);
-                    const u32 a = (cw[k >> 2] >> ((k & 3) * 8)) & 0xffu;
-                    const bool is_lit = (lit >> k) & 1u;
-                    uint2 d;
-                    if (DSMEM) d = reinterpret_cast<const uint2*>(dict)[bt];
-                    else d = __ldg(reinterpret_cast<const uint2*>(p.dict.table) + bt);
-                    const uint4 tok =
-                        make_uint4(a == 0u ? 0u : (is_lit ? bt : d.x), (a == 0u || is_lit) ? 0u : d.y, 0u, 0u);
-                    as.put(tok, a);
-                }
+                if (allv) assemble_fsst<true>(p, dict, r, cw, lit, as);
+                else assemble_fsst<false>(p, dict, r, cw, lit, as);
             }
         }
         area.thr_excl[lane] = thr;

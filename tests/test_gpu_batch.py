@@ -56,16 +56,18 @@ class BatchItem:
         np.testing.assert_array_equal(offs_h[:self.n + 1], self.ref.offsets)
         np.testing.assert_array_equal(out_h[:self.ref.total], self.ref.data)
 
-    def check(self):
+    def check(self, ctx=""):
         out_h = self.out.cpu().numpy()
         offs_h = self.offs.cpu().numpy().view(np.uint32)
-        assert np.all(out_h[self.capacity:] == GUARD), f"{self.col.name}: write past capacity"
-        assert np.all(offs_h[self.n + 1:] == 0xFFFFFFFF), f"{self.col.name}: write past offsets"
-        np.testing.assert_array_equal(offs_h[:self.n + 1], self.ref.offsets, err_msg=self.col.name)
+        name = f"{self.col.name} {ctx}"
+        assert np.all(out_h[self.capacity:] == GUARD), f"{name}: write past capacity"
+        assert np.all(offs_h[self.n + 1:] == 0xFFFFFFFF), f"{name}: write past offsets"
         data = out_h[:self.ref.total]
-        if not np.array_equal(data, self.ref.data):
-            bad = int(np.nonzero(data != self.ref.data)[0][0])
-            raise AssertionError(f"{self.col.name}: first differing byte at {bad} of {data.size}")
+        bad_data = np.nonzero(data != self.ref.data)[0]
+        np.testing.assert_array_equal(offs_h[:self.n + 1], self.ref.offsets,
+                                      err_msg=f"{name} ({bad_data.size} bytes differ too)")
+        if bad_data.size:
+            raise AssertionError(f"{name}: first differing byte at {int(bad_data[0])} of {data.size}")
 
 
 def mixed_items(fp, seed=0):
@@ -114,7 +116,7 @@ def test_batch_every_config_matches_oracle(fp, seed):
         assert np.all(sts == 0)
         for it, t in zip(items, tot):
             assert int(t) == it.ref.total
-            it.check()
+            it.check(f"config {cfg}")
         plan.destroy()
 
 
