@@ -235,14 +235,30 @@ def run_ours(args, rank, world, local_rank):
     out = torch.empty(total, dtype=torch.uint8, device=dev)
     offs = torch.empty(n + 1, dtype=torch.int32, device=dev)
     codes_bytes = codes.numel()
+    sidecar = None
+    if args.sidecar:
+        # the stored-sidecar decode: the table is computed once beforehand
+        # (untimed), as a column would carry it from compression
+        sidecar = fp.SidecarColumn(codec, d, codes, co, n)
+        sidecar.build(sh)
+        if sidecar.status_bits() != 0:
+            raise RuntimeError(f"sidecar build: data-error bits {sidecar.status_bits()}")
 
     def step():
-        fp.decode(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
-                  offs.data_ptr(), sh)
+        if sidecar is not None:
+            sidecar.decode(out, offs, sh)
+        else:
+            fp.decode(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
+                      offs.data_ptr(), sh)
+
+    def status_ok():
+        if sidecar is not None:
+            return sidecar.status_bits() == 0
+        return fp.sync_status(sh) == fp.OK
 
     # correctness gate on a sample before timing (the full oracle check lives in the tests)
     step()
-    if fp.sync_status(sh) != fp.OK:
+    if not status_ok():
         raise RuntimeError(fp.last_error())
 
     gpu_id = "0"
@@ -281,8 +297,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     total_ms = t0.elapsed_time(t1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    st = fp.sync_status(sh)
-    if st != fp.OK:
+    if not status_ok():
         raise RuntimeError(fp.last_error())
     total_ms, all_bytes = combine_ranks(dist, total_ms, float(total), dev)
 
@@ -402,6 +417,12 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "gpu_launches": vinfo["launches_per_call"] * args.steps,   # index pass (+ reduce in the same launch, tile scan) + decode
     }
+    if sidecar is not None:
+        line["metric"] = "decoded GB/s from a stored sidecar (tile output offsets computed beforehand, untimed)"
+        line["config"]["sidecar"] = {"tile_slots": fp.sidecar_tile_slots(codec), "entries": sidecar.entries}
+        line["config"].pop("variant")
+        line["roofline"]["traffic"] = None
+        line["gpu_launches"] = 3 * args.steps   # index pass, size check, decode
     line.update(extra)
     if "e2e" not in line:
         line["e2e"] = None
@@ -1113,6 +1134,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--quick", action="store_true", help="skip the baselines and the e2e leg")
+    ap.add_argument("--sidecar", action="store_true",
+                    help="single-column workloads: time fp_decode_sidecar on a table built beforehand (implies --quick)")
     ap.add_argument("--variant", type=int, default=-1, help="decode variant (-1: built-in default)")
     ap.add_argument("--n-strings", type=int, default=0, help="override the workload's string count")
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="served: length of the arrival process")
@@ -1128,6 +1151,10 @@ def main():
     rank, world, local_rank = env_rank()
     batched = args.workload in BATCH_WORKLOADS
     served = args.workload in SERVE_WORKLOADS
+    if args.sidecar:
+        if batched or served:
+            ap.error("--sidecar applies to the single-column workloads")
+        args.quick = True
     if args.impl == "reference":
         (run_batched_reference if batched else run_served_reference if served else run_reference)(args, rank, world)
     elif served:

@@ -44,6 +44,8 @@ def _load():
             lib.fpo_decode_mt.restype = I
             lib.fpo_unpack12.argtypes = [P, U64, P]
             lib.fpo_unpack12.restype = None
+            lib.fpo_sidecar.argtypes = [I, P, P, U32, P, U64, P, U32, U32, P, U64]
+            lib.fpo_sidecar.restype = U64
             _lib = lib
     return _lib
 
@@ -116,6 +118,19 @@ def decoded_size(codec, dict_data, dict_offsets, stream, code_offsets) -> tuple[
     r = lib.fpo_decode(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes,
                        _ptr(co), co.size - 1, None, 0, None, ctypes.byref(total), ctypes.byref(err))
     return r, int(total.value)
+
+
+def sidecar(codec: int, dict_data, dict_offsets, stream, code_offsets, tile: int) -> np.ndarray | None:
+    """The column's stored sidecar for tiles of ``tile`` slots (entry 0 the
+    decoded size, then one entry per tile); None for an invalid column."""
+    lib = _load()
+    dd, do, st, st_bytes, co = _args(codec, dict_data, dict_offsets, stream, code_offsets)
+    n_slots = st_bytes * 8 // {1: 16, 2: 12, 3: 8}[codec]
+    cap = n_slots // tile + 3
+    out = np.zeros(cap, np.uint64)
+    t = lib.fpo_sidecar(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), co.size - 1,
+                        tile, _ptr(out), cap)
+    return None if t == 0 else out[:1 + t]
 
 
 def unpack12(stream, n: int) -> np.ndarray:

@@ -241,3 +241,57 @@ int fpo_decode_mt(int codec, const uint8_t* dict_bytes, const uint32_t* dict_off
     if (err_bits) *err_bits = err;
     return status_of(err);
 }
+
+
+/*
+ * Stored sidecar of a column (paper Sec. 3.1: output positions recorded when
+ * the column was compressed, read by the decoder instead of computed).  The
+ * column's slots [c0, c1) (c0 = code_offsets[0], c1 = code_offsets[n]) are
+ * cut into tiles of `tile` slots aligned to multiples of `tile`: tile u
+ * starts at slot s_u = (c0 / tile + u) * tile, u = 0 .. T-1,
+ * T = max(1, ceil(c1 / tile) - c0 / tile).
+ *   entries[0]     = decoded size of the column;
+ *   entries[1 + u] = bytes produced by the column's slots before
+ *                    max(s_u, c0), with bit 63 set when slot s_u is the
+ *                    literal byte of an FSST-8 escape.
+ * The walk below is the decode's parse, slot by slot, recording the running
+ * byte count whenever a slot starts a tile.  Returns T, or 0 when the
+ * column is invalid or corrupt or entries has fewer than 1 + T elements.
+ */
+uint64_t fpo_sidecar(int codec, const uint8_t* dict_bytes, const uint32_t* dict_offsets, uint32_t n_entries,
+                     const uint8_t* stream, uint64_t stream_bytes, const uint32_t* code_offsets,
+                     uint32_t n_strings, uint32_t tile, uint64_t* entries, uint64_t max_entries) {
+    column_t c = {codec, dict_bytes, dict_offsets, n_entries, stream, 0, code_offsets};
+    int w = code_bits(codec);
+    if (!w || tile == 0) return 0;
+    c.n_slots = stream_bytes * 8 / (uint64_t)w;
+    unsigned err = 0;
+    if (check_column(&c, n_strings, &err) != FPO_OK) return 0;
+    const uint64_t c0 = code_offsets[0], c1 = code_offsets[n_strings];
+    const uint64_t first = c0 / tile, end = (c1 + tile - 1) / tile;
+    const uint64_t T = end > first ? end - first : 1;
+    if (1 + T > max_entries) return 0;
+    for (uint64_t u = 0; u < T; ++u) entries[1 + u] = 0;
+    uint64_t produced = 0;
+    for (uint32_t i = 0; i < n_strings; ++i) {
+        uint64_t j = code_offsets[i];
+        const uint64_t e = code_offsets[i + 1];
+        while (j < e) {
+            if (j % tile == 0 && j > c0) entries[1 + (j / tile - first)] = produced;
+            const uint32_t code = read_code(codec, stream, j);
+            if (codec == FPO_FSST8 && code == 255) {
+                if (j + 1 >= e) return 0;   /* escape without its literal */
+                /* the literal slot: it may start a tile too, flagged as a literal */
+                if ((j + 1) % tile == 0) entries[1 + ((j + 1) / tile - first)] = produced | (1ull << 63);
+                produced += 1;
+                j += 2;
+                continue;
+            }
+            if (code >= n_entries) return 0;
+            produced += dict_offsets[code + 1] - dict_offsets[code];
+            j += 1;
+        }
+    }
+    entries[0] = produced;
+    return T;
+}

@@ -80,13 +80,21 @@ def lib() -> ctypes.CDLL:
             L.fp_serve_release.argtypes = [P, U64]
             L.fp_serve_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
             L.fp_serve_destroy.argtypes = [P]
+            L.fp_sidecar_tile_slots.argtypes = [I]
+            L.fp_sidecar_tile_slots.restype = U32
+            L.fp_sidecar_entries.argtypes = [I, U64]
+            L.fp_sidecar_entries.restype = U64
+            L.fp_sidecar_scratch_bytes.argtypes = [I, U64]
+            L.fp_sidecar_scratch_bytes.restype = U64
+            L.fp_sidecar_build.argtypes = [I, P, P, U64, P, U32, P, U64, P, U64, P, P]
+            L.fp_decode_sidecar.argtypes = [I, P, P, U64, P, U32, P, U64, P, U64, P, P, U64, P, P]
             for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
                          "fp_decode_noalloc",
                          "fp_sync_status", "fp_variant_info", "fp_variant_select",
                          "fp_plan_create", "fp_plan_create_config", "fp_decode_batch", "fp_plan_sync_status",
                          "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info", "fp_serve_create",
                          "fp_serve_dict_put", "fp_serve_submit", "fp_serve_poll", "fp_serve_release",
-                         "fp_serve_stats", "fp_serve_destroy"):
+                         "fp_serve_stats", "fp_serve_destroy", "fp_sidecar_build", "fp_decode_sidecar"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib
@@ -215,6 +223,76 @@ def decode_noalloc(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offset
     st = lib().fp_decode_noalloc(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr,
                                  capacity, out_offsets_ptr, status_ptr, _stream(stream))
     return _check(st, "fp_decode_noalloc") if check else st
+
+
+# ---- stored sidecar (fastpair_sidecar.h) -----------------------------------
+
+def sidecar_tile_slots(codec: int) -> int:
+    return lib().fp_sidecar_tile_slots(codec)
+
+
+def sidecar_entries(codec: int, codes_bytes: int) -> int:
+    return lib().fp_sidecar_entries(codec, codes_bytes)
+
+
+def sidecar_scratch_bytes(codec: int, codes_bytes: int) -> int:
+    return lib().fp_sidecar_scratch_bytes(codec, codes_bytes)
+
+
+def sidecar_build(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                  sidecar_ptr: int, sidecar_entries: int, scratch_ptr: int, scratch_bytes: int, status_ptr: int,
+                  stream=None, check: bool = True) -> int:
+    """fp_sidecar_build: the column's stored table of tile output offsets."""
+    st = lib().fp_sidecar_build(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, sidecar_ptr,
+                                sidecar_entries, scratch_ptr, scratch_bytes, status_ptr, _stream(stream))
+    return _check(st, "fp_sidecar_build") if check else st
+
+
+def decode_sidecar(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                   sidecar_ptr: int, sidecar_entries: int, out_ptr: int, capacity: int, out_offsets_ptr: int,
+                   scratch_ptr: int, scratch_bytes: int, status_ptr: int, stream=None, check: bool = True) -> int:
+    """fp_decode_sidecar: decode from a stored sidecar (no reduce, no tile scan)."""
+    st = lib().fp_decode_sidecar(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, sidecar_ptr,
+                                 sidecar_entries, out_ptr, capacity, out_offsets_ptr, scratch_ptr, scratch_bytes,
+                                 status_ptr, _stream(stream))
+    return _check(st, "fp_decode_sidecar") if check else st
+
+
+class SidecarColumn:
+    """Device buffers for the stored-sidecar calls of one code buffer: the
+    sidecar (uint64 entries), the scratch and the status word, allocated
+    with torch.  `codes` is a uint8 CUDA tensor, `code_offsets` an int32 one."""
+
+    def __init__(self, codec: int, d: Dict, codes, code_offsets, n_strings: int, codes_bytes: int | None = None):
+        import torch
+        self.codec, self.d, self.codes, self.code_offsets, self.n_strings = codec, d, codes, code_offsets, n_strings
+        self.codes_bytes = codes.numel() * codes.element_size() if codes_bytes is None else codes_bytes
+        self.entries = sidecar_entries(codec, self.codes_bytes)
+        self.sidecar = torch.zeros(self.entries, dtype=torch.int64, device=codes.device)
+        self.scratch_bytes = sidecar_scratch_bytes(codec, self.codes_bytes)
+        self.scratch = torch.empty(self.scratch_bytes, dtype=torch.uint8, device=codes.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=codes.device)
+
+    def build(self, stream=None, check: bool = True) -> int:
+        return sidecar_build(self.codec, self.d, self.codes.data_ptr(), self.codes_bytes,
+                             self.code_offsets.data_ptr(), self.n_strings, self.sidecar.data_ptr(), self.entries,
+                             self.scratch.data_ptr(), self.scratch_bytes, self.status.data_ptr(), stream, check)
+
+    def decode(self, out, out_offsets, stream=None, check: bool = True, sidecar=None) -> int:
+        """Decode into torch tensors from this column's sidecar (or another
+        uint64 table of at least `entries` entries)."""
+        sc = self.sidecar if sidecar is None else sidecar
+        if sc.numel() < self.entries:
+            raise ValueError("sidecar table too short")
+        return decode_sidecar(self.codec, self.d, self.codes.data_ptr(), self.codes_bytes,
+                              self.code_offsets.data_ptr(), self.n_strings, sc.data_ptr(), self.entries,
+                              out.data_ptr() if out.numel() else 0, out.numel() * out.element_size(),
+                              out_offsets.data_ptr(), self.scratch.data_ptr(), self.scratch_bytes,
+                              self.status.data_ptr(), stream, check)
+
+    def status_bits(self) -> int:
+        """The last call's data-error bits (synchronises with the device)."""
+        return int(self.status.cpu().numpy().view(np.uint32)[0])
 
 
 def decoded_size(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfastpair.so")
 
-SOURCES = ["fp_api.cu", "fp_decode.cu", "fp_batch.cu", "fp_plain.cu", "fp_serve.cu"]
+SOURCES = ["fp_api.cu", "fp_decode.cu", "fp_batch.cu", "fp_plain.cu", "fp_serve.cu", "fp_sidecar.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--cudart", "shared",
               "-Xptxas", "-v", "-I", INCLUDE, "-I", CSRC]

@@ -52,3 +52,26 @@ def fsst8_escape_cases(name="fsst8_escapes.txt"):
         rhs = rhs.strip()
         out.append((_hex(lhs), None if rhs == "CORRUPT" else _hex(rhs)))
     return out
+
+
+def sidecar_cases(name="sidecar_small.txt"):
+    """Stored-sidecar fixtures: a column plus `tile` and the expected table."""
+    cases, cur = [], {}
+    for ln in _lines(name):
+        key, _, rest = ln.partition(" ")
+        if key == "end":
+            cases.append(cur)
+            cur = {}
+        elif key == "codec":
+            cur["codec"] = CODECS[rest.strip()]
+        elif key == "tokens":
+            cur["tokens"] = [bytes.fromhex(t) for t in rest.split()]
+        elif key == "code_offsets":
+            cur[key] = np.array([int(t) for t in rest.split()], np.uint32)
+        elif key == "stream":
+            cur[key] = _hex(rest)
+        elif key == "tile":
+            cur[key] = int(rest)
+        elif key == "expect_sidecar":
+            cur[key] = np.array([int(t) for t in rest.split()], np.uint64)
+    return cases
