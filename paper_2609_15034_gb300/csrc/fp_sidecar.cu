@@ -140,9 +140,8 @@ fp_status device_setup(int codec, int* sms) {
     return FP_OK;
 }
 
-// Arguments shared by both calls; fills p's column fields and the layout.
-fp_status check_sidecar_args(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
-                             const uint32_t* d_code_offsets, uint32_t n_strings, const void* d_sidecar,
+// Checks of the arguments both calls add to fp_decode's; fills the layout.
+fp_status check_sidecar_args(fp_codec codec, uint64_t codes_bytes, uint32_t n_strings, const void* d_sidecar,
                              uint64_t sidecar_entries, void* d_scratch, uint64_t scratch_bytes,
                              const uint32_t* d_status, Layout* L) {
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
@@ -160,9 +159,6 @@ fp_status check_sidecar_args(fp_codec codec, const fp_dict* dict, const void* d_
                     (unsigned long long)scratch_bytes, (unsigned long long)L->bytes);
     if (!d_status) return fail(FP_ERR_ARG, "d_status is NULL");
     if (reinterpret_cast<uintptr_t>(d_status) % 4) return fail(FP_ERR_ARG, "d_status not 4-byte aligned");
-    (void)dict;
-    (void)d_codes;
-    (void)d_code_offsets;
     return FP_OK;
 }
 
@@ -245,8 +241,8 @@ fp_status fp_sidecar_build(fp_codec codec, const fp_dict* dict, const void* d_co
     fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, nullptr, 0, nullptr, false);
     if (st != FP_OK) return st;
     Layout L;
-    st = check_sidecar_args(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_sidecar,
-                            sidecar_entries, d_scratch, scratch_bytes, d_status, &L);
+    st = check_sidecar_args(codec, codes_bytes, n_strings, d_sidecar, sidecar_entries, d_scratch, scratch_bytes,
+                            d_status, &L);
     if (st != FP_OK) return st;
     int sms = 0;
     st = device_setup(codec, &sms);
@@ -278,8 +274,8 @@ fp_status fp_decode_sidecar(fp_codec codec, const fp_dict* dict, const void* d_c
                                 d_out_offsets, true);
     if (st != FP_OK) return st;
     Layout L;
-    st = check_sidecar_args(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_sidecar,
-                            sidecar_entries, d_scratch, scratch_bytes, d_status, &L);
+    st = check_sidecar_args(codec, codes_bytes, n_strings, d_sidecar, sidecar_entries, d_scratch, scratch_bytes,
+                            d_status, &L);
     if (st != FP_OK) return st;
     int sms = 0;
     st = device_setup(codec, &sms);
