@@ -46,6 +46,8 @@ def _load():
             lib.fpo_unpack12.restype = None
             lib.fpo_sidecar.argtypes = [I, P, P, U32, P, U64, P, U32, U32, P, U64]
             lib.fpo_sidecar.restype = U64
+            lib.fpo_decode_rows.argtypes = [I, P, P, U32, P, U64, P, U32, P, U32, P, U64, P, P, P]
+            lib.fpo_decode_rows.restype = I
             _lib = lib
     return _lib
 
@@ -131,6 +133,29 @@ def sidecar(codec: int, dict_data, dict_offsets, stream, code_offsets, tile: int
     t = lib.fpo_sidecar(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), co.size - 1,
                         tile, _ptr(out), cap)
     return None if t == 0 else out[:1 + t]
+
+
+def decode_rows(codec: int, dict_data, dict_offsets, stream, code_offsets, row_ids,
+                capacity: int | None = None) -> OracleResult:
+    """Decode the strings row_ids (in that order) of a column."""
+    lib = _load()
+    dd, do, st, st_bytes, co = _args(codec, dict_data, dict_offsets, stream, code_offsets)
+    rows = np.ascontiguousarray(row_ids, np.uint32)
+    m = int(rows.size)
+    rp = _ptr(rows if m else np.zeros(1, np.uint32))
+    total = ctypes.c_uint64(0)
+    err = ctypes.c_uint(0)
+    if capacity is None:
+        r = lib.fpo_decode_rows(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), co.size - 1,
+                                rp, m, None, 0, None, ctypes.byref(total), ctypes.byref(err))
+        if r not in (OK, ERR_OVERFLOW):
+            return OracleResult(r, err.value, total.value, None, None)
+        capacity = total.value
+    out = np.zeros(max(capacity, 1), np.uint8)
+    offs = np.zeros(m + 1, np.uint32)
+    r = lib.fpo_decode_rows(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), co.size - 1,
+                            rp, m, _ptr(out), capacity, _ptr(offs), ctypes.byref(total), ctypes.byref(err))
+    return OracleResult(r, err.value, total.value, out[:min(total.value, capacity)], offs)
 
 
 def unpack12(stream, n: int) -> np.ndarray:

@@ -295,3 +295,39 @@ uint64_t fpo_sidecar(int codec, const uint8_t* dict_bytes, const uint32_t* dict_
     entries[0] = produced;
     return T;
 }
+
+
+/*
+ * Selective decode: the strings row_ids[0..m-1] of a column (any order,
+ * repeats allowed) decoded one after another into out, with
+ * out_offsets[0] = 0 and out_offsets[k+1] = bytes after row_ids[k].  This is
+ * random access to single strings, which FSST-family codecs allow because a
+ * string's codes decode on their own (paper Sec. 1 and Sec. 2.1).  Each row
+ * is decoded by the same walk as fpo_decode.  A row id >= n_strings is an
+ * argument error.  Returns a status as fpo_decode.
+ */
+int fpo_decode_rows(int codec, const uint8_t* dict_bytes, const uint32_t* dict_offsets, uint32_t n_entries,
+                    const uint8_t* stream, uint64_t stream_bytes, const uint32_t* code_offsets,
+                    uint32_t n_strings, const uint32_t* row_ids, uint32_t m, uint8_t* out, uint64_t out_capacity,
+                    uint32_t* out_offsets, uint64_t* total, unsigned* err_bits) {
+    column_t c = {codec, dict_bytes, dict_offsets, n_entries, stream,
+                  code_bits(codec) ? stream_bytes * 8 / (uint64_t)code_bits(codec) : 0, code_offsets};
+    unsigned err = 0;
+    int st = check_column(&c, n_strings, &err);
+    if (err_bits) *err_bits = err;
+    if (st != FPO_OK) return st;
+    for (uint32_t k = 0; k < m; ++k)
+        if (row_ids[k] >= n_strings) return FPO_ERR_ARG;
+    uint64_t pos = 0;
+    if (out_offsets) out_offsets[0] = 0;
+    for (uint32_t k = 0; k < m; ++k) {
+        const uint32_t r = row_ids[k];
+        pos += decode_range(&c, r, r + 1, out ? out + pos : NULL, pos, out ? out_capacity : 0, NULL, &err);
+        if (out_offsets) out_offsets[k + 1] = (uint32_t)pos;
+    }
+    if (out && pos > out_capacity) err |= FPO_BIT_CAPACITY;
+    if (pos > 0x7fffffffull) err |= FPO_BIT_OVERFLOW;
+    if (total) *total = pos;
+    if (err_bits) *err_bits = err;
+    return status_of(err);
+}
