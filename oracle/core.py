@@ -127,7 +127,7 @@ def sidecar(codec: int, dict_data, dict_offsets, stream, code_offsets, tile: int
     decoded size, then one entry per tile); None for an invalid column."""
     lib = _load()
     dd, do, st, st_bytes, co = _args(codec, dict_data, dict_offsets, stream, code_offsets)
-    n_slots = st_bytes * 8 // {1: 16, 2: 12, 3: 8}[codec]
+    n_slots = st_bytes * 8 // {1: 16, 2: 12, 3: 8, 4: 12}[codec]
     cap = n_slots // tile + 3
     out = np.zeros(cap, np.uint64)
     t = lib.fpo_sidecar(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), co.size - 1,

@@ -12,7 +12,10 @@
  *   - Codec formats (Sec. 2.1): OnPair-16 = 16-bit codes, OnPair-12 = 12-bit
  *     codes, both into dictionaries of tokens of at most 16 bytes; FSST-8 =
  *     byte codes into a 255-symbol table of tokens of at most 8 bytes, where
- *     the reserved escape code 255 is followed by one literal byte.
+ *     the reserved escape code 255 is followed by one literal byte; FSST-12
+ *     = 12-bit codes into a table of up to 4,096 symbols of at most 8 bytes,
+ *     with no escape (the paper's escape-free variant, stored like
+ *     OnPair-12).
  *   - Output (Sec. 5): a variable-length string array: byte-packed string
  *     data plus an array of fixed-width offsets (uint32 here).
  *
@@ -33,14 +36,15 @@
 #include <string.h>
 #include <pthread.h>
 
-enum { FPO_ONPAIR16 = 1, FPO_ONPAIR12 = 2, FPO_FSST8 = 3 };
+enum { FPO_ONPAIR16 = 1, FPO_ONPAIR12 = 2, FPO_FSST8 = 3, FPO_FSST12 = 4 };
 enum { FPO_OK = 0, FPO_ERR_ARG = 1, FPO_ERR_CORRUPT = 4, FPO_ERR_CAPACITY = 5,
        FPO_ERR_OVERFLOW = 6 };
 /* error kinds reported as a bit set */
 enum { FPO_BIT_CORRUPT = 1, FPO_BIT_CAPACITY = 2, FPO_BIT_OVERFLOW = 4 };
 
 static int code_bits(int codec) {
-    return codec == FPO_ONPAIR16 ? 16 : codec == FPO_ONPAIR12 ? 12 : codec == FPO_FSST8 ? 8 : 0;
+    return codec == FPO_ONPAIR16 ? 16 : (codec == FPO_ONPAIR12 || codec == FPO_FSST12) ? 12
+                                      : codec == FPO_FSST8 ? 8 : 0;
 }
 
 /* Read stream bit b (LSB-first within each byte). */
@@ -53,7 +57,7 @@ static uint32_t read_code(int codec, const uint8_t* stream, uint64_t s) {
     if (codec == FPO_ONPAIR16) {
         return (uint32_t)stream[2 * s] | ((uint32_t)stream[2 * s + 1] << 8);
     }
-    if (codec == FPO_ONPAIR12) {
+    if (codec == FPO_ONPAIR12 || codec == FPO_FSST12) {
         uint32_t c = 0;
         for (unsigned k = 0; k < 12; ++k) c |= read_bit(stream, 12 * s + k) << k;
         return c;
@@ -113,8 +117,9 @@ static uint64_t decode_range(const column_t* c, uint32_t s0, uint32_t s1, uint8_
 static int check_column(const column_t* c, uint32_t n_strings, unsigned* err) {
     int w = code_bits(c->codec);
     if (!w) return FPO_ERR_ARG;
-    uint32_t max_len = c->codec == FPO_FSST8 ? 8 : 16;
-    uint32_t max_entries = c->codec == FPO_ONPAIR16 ? 65536u : c->codec == FPO_ONPAIR12 ? 4096u : 255u;
+    uint32_t max_len = (c->codec == FPO_FSST8 || c->codec == FPO_FSST12) ? 8 : 16;
+    uint32_t max_entries = c->codec == FPO_ONPAIR16 ? 65536u
+                           : (c->codec == FPO_ONPAIR12 || c->codec == FPO_FSST12) ? 4096u : 255u;
     if (c->n_entries == 0 || c->n_entries > max_entries) return FPO_ERR_ARG;
     for (uint32_t e = 0; e < c->n_entries; ++e) {
         uint32_t L = c->dict_offsets[e + 1] - c->dict_offsets[e];

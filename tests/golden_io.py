@@ -4,7 +4,7 @@ import os
 import numpy as np
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-CODECS = {"onpair16": 1, "onpair12": 2, "fsst8": 3}
+CODECS = {"onpair16": 1, "onpair12": 2, "fsst8": 3, "fsst12": 4}
 
 
 def _lines(name):
