@@ -21,7 +21,7 @@
  *                   max(s_u, c0), in bits 0..62; bit 63 = 1 if slot s_u is
  *                   the literal byte of an FSST-8 escape (always 0 for
  *                   OnPair and for u = 0).
- *   Entries after 1 + T - 1 are not read.  The table depends only on the
+ *   Entries after entry T are not read.  The table depends only on the
  *   codes, code_offsets and the dictionary's token lengths.
  *
  * Scratch: both calls take a caller-owned device scratch buffer of at least
