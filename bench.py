@@ -33,6 +33,9 @@ WORKLOADS = {
                   "FSST-8 with escapes, 255 URL/identifier symbols, 16M lognormal strings (median 40 B)"),
     "onpair16_100k": (synth.ONPAIR16, 100_000,
                       "OnPair-16, 65,536-entry dictionary, 100k strings of 1-40 codes, Zipf(1.1)"),
+    "fsst12_16m": (synth.FSST12, 16_000_000,
+                   "FSST-12 (escape-free 12-bit codes), 4,096 URL/identifier symbols of 1-8 B, 16M lognormal "
+                   "strings (median 40 B), Zipf(1.0)"),
 }
 # batched workloads: name -> (chunks, smallest and largest decoded chunk size, description)
 BATCH_WORKLOADS = {
@@ -227,6 +230,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     d = fp.Dict(codec, col.dictionary.data, col.dictionary.offsets, sh)
+    if args.width:
+        d.set_width(args.width)
     codes = torch.from_numpy(col.stream).to(dev)
     co = torch.from_numpy(col.code_offsets.view(np.int32)).to(dev)
     st, total = fp.decoded_size_tensors(codec, d, codes, co, n, sh)
@@ -398,8 +403,8 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
-    var = fp.variant_for(codec, codes_bytes)
-    vinfo = dict(fp.variant_info(codec, var), index=var)
+    var = fp.variant_for_dict(d, codes_bytes)
+    vinfo = dict(fp.variant_info(codec, var), index=var, read_width=fp.variant_width(codec, var))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -1137,6 +1142,8 @@ def main():
     ap.add_argument("--sidecar", action="store_true",
                     help="single-column workloads: time fp_decode_sidecar on a table built beforehand (implies --quick)")
     ap.add_argument("--variant", type=int, default=-1, help="decode variant (-1: built-in default)")
+    ap.add_argument("--width", type=int, default=0, choices=[0, 8, 16],
+                    help="OnPair dictionary read width (0: the dictionary's own, by the split-read rule)")
     ap.add_argument("--n-strings", type=int, default=0, help="override the workload's string count")
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="served: length of the arrival process")
     ap.add_argument("--serve-streams", type=int, default=4, help="served: concurrent waves")

@@ -14,11 +14,13 @@
  *   FP_ONPAIR12  12-bit codes, up to 4,096 tokens of 1..16 bytes.
  *   FP_FSST8     8-bit codes, up to 255 tokens of 1..8 bytes; code 255 is the
  *                escape: the slot after it holds one literal byte.
+ *   FP_FSST12    12-bit codes, up to 4,096 tokens of 1..8 bytes, no escape
+ *                (the escape-free variant the paper decodes).
  *
  * Stored layouts:
  *   - OnPair-16: little-endian uint16 per code.
- *   - OnPair-12: LSB-first bitstream; code i occupies stream bits
- *     [12 i, 12 i + 12), stream bit b is bit (b mod 8) of byte b / 8.
+ *   - OnPair-12 and FSST-12: LSB-first bitstream; code i occupies stream
+ *     bits [12 i, 12 i + 12), stream bit b is bit (b mod 8) of byte b / 8.
  *   - FSST-8: one byte per slot (codes and the literal bytes after escapes).
  *   A "slot" is one code position (for FSST-8 a literal byte is a slot too).
  *
@@ -51,7 +53,8 @@ typedef struct CUstream_st* fp_stream_t; /* same type as cudaStream_t */
 typedef enum fp_codec {
     FP_ONPAIR16 = 1,
     FP_ONPAIR12 = 2,
-    FP_FSST8 = 3
+    FP_FSST8 = 3,
+    FP_FSST12 = 4
 } fp_codec;
 
 typedef enum fp_status {
@@ -66,7 +69,11 @@ typedef enum fp_status {
     FP_ERR_OVERFLOW = 6,  /* decoded size exceeds 2^31 - 1 (int32 offsets)    */
     FP_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up               */
     FP_ERR_BUSY = 8,      /* resource busy / budget exhausted                 */
-    FP_ERR_NOT_READY = 9  /* result not available yet                         */
+    FP_ERR_NOT_READY = 9, /* result not available yet                         */
+    FP_ERR_INTERNAL = 10  /* a decoder self-check failed: a warp tile's byte  */
+                          /* total, recomputed by the decode, disagrees with  */
+                          /* the offsets its length pass scanned (the output  */
+                          /* is then wrong; writes stay in bounds)            */
 } fp_status;
 
 /* Opaque, library-owned, device-resident dictionary. */
@@ -84,20 +91,48 @@ typedef struct fp_dict fp_dict;
  *   h_bytes     host, concatenated token bytes (may be NULL only if every
  *               token is empty, which is itself invalid).
  *   h_offsets   host, n_entries + 1 non-decreasing uint32 offsets.
- *   n_entries   1..65,536 (OnPair-16), 1..4,096 (OnPair-12), 1..255 (FSST-8).
+ *   n_entries   1..65,536 (OnPair-16), 1..4,096 (OnPair-12, FSST-12),
+ *               1..255 (FSST-8).
  *   stream      stream for the uploads; the call synchronises it before it
  *               returns (the host buffers may be reused at once).
  *   out         receives the dictionary handle.
  *
+ * OnPair dictionaries are also stored as two planes (bytes 0-7 and 8-15 of
+ * every entry, paper Sec. 3.2) and carry a read width W: 8 = split read
+ * (the low plane for every token, the high plane only for tokens longer
+ * than 8 bytes), 16 = whole entries.  The upload sets W by the paper's rule
+ * (Sec. 4.3: W = 8 unless more than 60 % of the tokens exceed 8 bytes)
+ * applied to the dictionary's own entries; fp_dict_set_width overrides it,
+ * e.g. with fp_width_for_histogram of a column's token-length histogram.
+ *
  * Errors: FP_ERR_ARG if a token length is outside 1..16 (OnPair) or 1..8
- * (FSST-8), n_entries is out of range or a pointer is NULL; FP_ERR_NOMEM;
- * FP_ERR_CUDA.  Duplicate tokens are allowed.
+ * (FSST-8, FSST-12), n_entries is out of range or a pointer is NULL;
+ * FP_ERR_NOMEM; FP_ERR_CUDA.  Duplicate tokens are allowed.
  */
 fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t* h_offsets,
                          uint32_t n_entries, fp_stream_t stream, fp_dict** out);
 
 /* Release a dictionary (synchronises the device first).  NULL is a no-op. */
 fp_status fp_dict_free(fp_dict* dict);
+
+/*
+ * fp_width_for_histogram -- the paper's split-read rule (Sec. 4.3): 16 when
+ * more than 60 % of the counted tokens are longer than 8 bytes, else 8.
+ * hist[L] is the number of tokens of L bytes (L = 0..16) -- typically a
+ * column's token occurrences, which the encoder holds.  An all-zero
+ * histogram gives 8.
+ */
+int fp_width_for_histogram(const uint64_t* hist17);
+
+/*
+ * fp_dict_set_width / fp_dict_width -- the dictionary read width fp_decode
+ * uses for this dictionary when no variant is selected: 8 (split read) or
+ * 16 (whole entries).  FSST codecs have 8-byte entries and accept only 8.
+ * FP_ERR_ARG for other values.  Not synchronised with decodes in flight
+ * (set it before enqueueing the decodes that should use it).
+ */
+fp_status fp_dict_set_width(fp_dict* dict, int width);
+int fp_dict_width(const fp_dict* dict);
 
 /*
  * fp_decode -- decode one column into Arrow-style bytes plus offsets.
@@ -149,6 +184,41 @@ fp_status fp_decoded_size(fp_codec codec, const fp_dict* dict, const void* d_cod
                           fp_stream_t stream, uint64_t* h_total);
 
 /*
+ * Selective decode (paper Sec. 1 and Sec. 2.1: strings of FSST-family
+ * columns decode independently, which allows random access): the strings
+ * d_row_ids[0 .. n_rows) of a column, in that order, into Arrow-style
+ * output -- d_out_bytes[d_out_offsets[k] .. d_out_offsets[k+1]) is string
+ * d_row_ids[k].  Row ids may repeat and need not be sorted.
+ *
+ * The calls gather the selected rows' codes into one contiguous stream in
+ * the stream's workspace (a row-length pass, a scan of the row lengths and
+ * a compaction) and decode that stream with fp_decode's kernels.
+ *
+ * fp_rows_size -- synchronous: *h_slots receives the number of code slots
+ *   the selected rows hold (the `selected_slots` fp_decode_rows needs) and
+ *   *h_bytes their decoded size.  Returns the data status as
+ *   fp_sync_status would.
+ *
+ * fp_decode_rows -- asynchronous.  selected_slots >= the rows' code slots
+ *   (fp_rows_size); it sizes the workspace.  Inputs as fp_decode, plus
+ *   d_row_ids (device, n_rows uint32, 4-byte aligned); d_out_offsets has
+ *   n_rows + 1 entries.
+ *
+ * Data errors (fp_sync_status): a row id >= n_strings, a selected row
+ * whose code_offsets decrease or pass the code buffer, and the errors of
+ * fp_decode in a selected row -> FP_ERR_CORRUPT; more selected slots than
+ * selected_slots -> FP_ERR_CAPACITY (or FP_ERR_CORRUPT); the output and
+ * overflow checks as fp_decode.  Rows that are not selected are not read.
+ */
+fp_status fp_rows_size(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                       const uint32_t* d_code_offsets, uint32_t n_strings, const uint32_t* d_row_ids,
+                       uint32_t n_rows, fp_stream_t stream, uint64_t* h_slots, uint64_t* h_bytes);
+fp_status fp_decode_rows(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                         const uint32_t* d_code_offsets, uint32_t n_strings, const uint32_t* d_row_ids,
+                         uint32_t n_rows, uint64_t selected_slots, uint8_t* d_out_bytes, uint64_t out_capacity,
+                         uint32_t* d_out_offsets, fp_stream_t stream);
+
+/*
  * fp_decode_plain -- baseline decoder with one thread per string.
  *
  * Same arguments, result and error behaviour as fp_decode.  Each thread
@@ -165,13 +235,30 @@ fp_status fp_decode_plain(fp_codec codec, const fp_dict* dict, const void* d_cod
 /*
  * fp_sync_status -- synchronise `stream`, then read and clear its sticky
  * data-error status.  Returns FP_OK or, by priority, FP_ERR_TIMEOUT,
- * FP_ERR_CORRUPT, FP_ERR_CAPACITY, FP_ERR_OVERFLOW; FP_ERR_CUDA if the
- * synchronisation itself failed.
+ * FP_ERR_INTERNAL, FP_ERR_CORRUPT, FP_ERR_CAPACITY, FP_ERR_OVERFLOW;
+ * FP_ERR_CUDA if the synchronisation itself failed.
  */
 fp_status fp_sync_status(fp_stream_t stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* fp_last_error(void);
+
+/*
+ * fp_debug_stall_next -- failure-detection test hook (no counterpart in the
+ * paper): make the next fp_decode on `stream` give up a bounded wait on
+ * purpose, without any fault.  That call skips the first ticket of its
+ * ticketed pass (the tile scan of the warp-tile decoder, or the decode of
+ * the block pipeline), so the first look-back word is never published and
+ * the look-back that needs it polls it `spin_limit` times (1..2^20; the
+ * built-in limit is 2^20 polls with back-off), then gives up.  The call
+ * reports FP_ERR_TIMEOUT through fp_sync_status; its output is unspecified
+ * but every write stays in bounds.  Both settings end with that call: the
+ * next decode on the stream is normal.
+ *
+ * The stream must already have a workspace (one earlier fp_decode on it);
+ * FP_ERR_ARG otherwise.  Stream-ordered, asynchronous.
+ */
+fp_status fp_debug_stall_next(fp_stream_t stream, uint32_t spin_limit);
 
 /*
  * fp_decode_noalloc -- fp_decode for callers that cannot allocate.
@@ -189,14 +276,17 @@ const char* fp_last_error(void);
  *   d_status   device, one uint32 written (stream-ordered) with the call's
  *              data-error bits: 0 = OK; 1 = corrupt input, 2 = decoded size
  *              above out_capacity, 4 = above 2^31-1, 8 = a bounded device
- *              wait gave up.  fp_sync_status does not report these calls.
+ *              wait gave up, 16 = a decoder self-check failed (see
+ *              FP_ERR_INTERNAL).  fp_sync_status does not report these calls.
  *
  * Limits and sharing:
  *   - unless a variant is selected (fp_variant_select), this call uses the
  *     block pipeline, whose scratch covers a code buffer of up to about
  *     357M slots (OnPair codecs; 715M for FSST-8); a selected warp-tile
- *     variant covers about 26.8M.  Larger inputs return FP_ERR_ARG with the
- *     limit in fp_last_error() -- use fp_decode for them.
+ *     variant covers about 26.8M slots with 16 slots per lane (512-slot
+ *     tiles) and about 53.7M with 32 slots per lane (FSST-8's 1,024-slot
+ *     tiles).  Larger inputs return FP_ERR_ARG with the limit in
+ *     fp_last_error() -- use fp_decode for them.
  *   - the first call on a device looks up and clears the array
  *     (synchronously); make that first call before any stream capture.
  *   - every call, on any stream, shares the one array per device: calls
@@ -284,7 +374,7 @@ typedef struct fp_plan_info_t {
     uint32_t grid;                 /* blocks of the persistent launch           */
     uint32_t index_blocks;         /* blocks of the index pass                  */
     uint32_t from_cache;           /* 1 if the configuration came from the file */
-    uint32_t reserved;
+    uint32_t slots_per_thread_fsst12;  /* FSST-12 (0: the configuration has no FSST-12 queue) */
     uint64_t total_tiles;
     uint64_t layout_bytes;         /* device bytes of the plan's tables         */
     float tune_ms[8];              /* tuning time per configuration, -1 = untimed */
@@ -299,7 +389,10 @@ fp_status fp_plan_destroy(fp_plan* plan);
  * FSST-8), blocks per SM, and 1 for the warp-tile decoder (index pass,
  * reduce, tile scan and a persistent decode: four launches) or 0 for the
  * block pipeline (index pass and the persistent decode).  Out pointers may be
- * NULL. */
+ * NULL.  FSST-12 chunks are decoded only by the warp-tile configurations
+ * (with the OnPair-12 slots per thread); fp_plan_create skips the others for
+ * plans that hold FSST-12 chunks and fp_plan_create_config rejects them with
+ * FP_ERR_ARG. */
 int fp_batch_config_count(void);
 fp_status fp_batch_config_info(int config, uint32_t* slots_per_thread3, uint32_t* blocks_per_sm,
                                uint32_t* warp_tiles);
@@ -410,7 +503,8 @@ fp_status fp_serve_destroy(fp_server* server);
  *                   may be NULL.
  * fp_variant_select make variant v the one fp_decode uses for the codec in
  *                   this process (v = -1 restores the built-in defaults,
- *                   which depend on the size of the code buffer).
+ *                   which depend on the size of the code buffer and on the
+ *                   dictionary's read width).
  * fp_variant_selected  the variant selected for the codec, or with none
  *                   selected the default for large code buffers.
  * fp_variant_for    the variant fp_decode uses for a code buffer of
@@ -422,6 +516,15 @@ fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* sl
 fp_status fp_variant_select(fp_codec codec, int v);
 int fp_variant_selected(fp_codec codec);
 int fp_variant_for(fp_codec codec, uint64_t codes_bytes);
+
+/* The variant fp_decode uses with this dictionary (its codec and read
+ * width) for a code buffer of codes_bytes bytes; -1 for NULL.  fp_variant_for
+ * answers for read width 8. */
+int fp_variant_for_dict(const fp_dict* dict, uint64_t codes_bytes);
+
+/* Dictionary read width of variant v (16: whole entries, 8: split read);
+ * 0 for an unknown codec or variant. */
+int fp_variant_width(fp_codec codec, int v);
 
 #ifdef __cplusplus
 }

@@ -11,8 +11,8 @@
  * from a stored table and runs neither pass.
  *
  * Sidecar format (uint64 entries, little-endian, in device memory):
- *   S = fp_sidecar_tile_slots(codec) code slots per tile (512 for OnPair-16
- *   and OnPair-12, 1024 for FSST-8).  With c0 = code_offsets[0] and
+ *   S = fp_sidecar_tile_slots(codec) code slots per tile (512 for OnPair-16,
+ *   OnPair-12 and FSST-12, 1024 for FSST-8).  With c0 = code_offsets[0] and
  *   c1 = code_offsets[n_strings], the column's tiles are
  *   u = 0 .. T-1, T = max(1, ceil(c1 / S) - floor(c0 / S)), tile u starting
  *   at slot s_u = (floor(c0 / S) + u) * S.
@@ -32,13 +32,17 @@
  * Status: d_status is one device uint32 that the call clears and then ORs
  * its data-error bits into, stream-ordered: 1 = corrupt input (as
  * fp_decode), 2 = decoded size above out_capacity, 4 = above 2^31-1, 8 = a
- * bounded device wait gave up.  The host-side return value covers argument
- * errors and launch failures only, as for fp_decode.
+ * bounded device wait gave up, 16 = the table disagrees with the code
+ * stream (fp_decode_sidecar: some tile's byte total, recomputed from its
+ * codes, does not bring its entry to the next one).  The host-side return
+ * value covers argument errors and launch failures only, as for fp_decode.
  *
- * A sidecar that does not belong to the column gives wrong output, not an
- * error: the decode trusts it, as the paper's does.  Every write still stays
- * inside [0, out_capacity) of d_out_bytes and inside the n_strings + 1
- * entries of d_out_offsets.
+ * A sidecar that does not belong to the column gives wrong output: the
+ * decode places bytes where the table says, as the paper's does, and flags
+ * the disagreement with bit 16 (it does not catch a table whose entries are
+ * consistent with the codes but belong to other string boundaries).  Every
+ * write still stays inside [0, out_capacity) of d_out_bytes and inside the
+ * n_strings + 1 entries of d_out_offsets.
  */
 #ifndef FASTPAIR_SIDECAR_H
 #define FASTPAIR_SIDECAR_H

@@ -18,15 +18,15 @@ import threading
 
 import numpy as np
 
-ONPAIR16, ONPAIR12, FSST8 = 1, 2, 3
-CODEC_IDS = {"onpair16": ONPAIR16, "onpair12": ONPAIR12, "fsst8": FSST8}
-CODE_BITS = {ONPAIR16: 16, ONPAIR12: 12, FSST8: 8}
+ONPAIR16, ONPAIR12, FSST8, FSST12 = 1, 2, 3, 4
+CODEC_IDS = {"onpair16": ONPAIR16, "onpair12": ONPAIR12, "fsst8": FSST8, "fsst12": FSST12}
+CODE_BITS = {ONPAIR16: 16, ONPAIR12: 12, FSST8: 8, FSST12: 12}
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_CORRUPT, ERR_CAPACITY, ERR_OVERFLOW, ERR_TIMEOUT, ERR_BUSY, \
-    ERR_NOT_READY = range(10)
+    ERR_NOT_READY, ERR_INTERNAL = range(11)
 STATUS_NAMES = {0: "FP_OK", 1: "FP_ERR_ARG", 2: "FP_ERR_CUDA", 3: "FP_ERR_NOMEM", 4: "FP_ERR_CORRUPT",
                 5: "FP_ERR_CAPACITY", 6: "FP_ERR_OVERFLOW", 7: "FP_ERR_TIMEOUT", 8: "FP_ERR_BUSY",
-                9: "FP_ERR_NOT_READY"}
+                9: "FP_ERR_NOT_READY", 10: "FP_ERR_INTERNAL"}
 
 _lock = threading.Lock()
 _lib = None
@@ -59,6 +59,9 @@ def lib() -> ctypes.CDLL:
             L.fp_decoded_size.argtypes = [I, P, P, U64, P, U32, P, ctypes.POINTER(U64)]
             L.fp_decode_noalloc.argtypes = [I, P, P, U64, P, U32, P, U64, P, P, P]
             L.fp_sync_status.argtypes = [P]
+            L.fp_debug_stall_next.argtypes = [P, U32]
+            L.fp_rows_size.argtypes = [I, P, P, U64, P, U32, P, U32, P, ctypes.POINTER(U64), ctypes.POINTER(U64)]
+            L.fp_decode_rows.argtypes = [I, P, P, U64, P, U32, P, U32, U64, P, U64, P, P]
             L.fp_last_error.restype = ctypes.c_char_p
             L.fp_variant_count.argtypes = [I]
             L.fp_variant_info.argtypes = [I, I, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32),
@@ -66,6 +69,11 @@ def lib() -> ctypes.CDLL:
             L.fp_variant_select.argtypes = [I, I]
             L.fp_variant_selected.argtypes = [I]
             L.fp_variant_for.argtypes = [I, U64]
+            L.fp_variant_for_dict.argtypes = [P, U64]
+            L.fp_variant_width.argtypes = [I, I]
+            L.fp_width_for_histogram.argtypes = [P]
+            L.fp_dict_set_width.argtypes = [P, I]
+            L.fp_dict_width.argtypes = [P]
             L.fp_plan_create.argtypes = [ctypes.POINTER(Chunk), U32, ctypes.c_char_p, P, ctypes.POINTER(P)]
             L.fp_plan_create_config.argtypes = [ctypes.POINTER(Chunk), U32, I, P, ctypes.POINTER(P)]
             L.fp_decode_batch.argtypes = [P, P]
@@ -90,7 +98,8 @@ def lib() -> ctypes.CDLL:
             L.fp_decode_sidecar.argtypes = [I, P, P, U64, P, U32, P, U64, P, U64, P, P, U64, P, P]
             for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
                          "fp_decode_noalloc",
-                         "fp_sync_status", "fp_variant_info", "fp_variant_select",
+                         "fp_sync_status", "fp_debug_stall_next", "fp_variant_info", "fp_variant_select",
+                         "fp_dict_set_width", "fp_rows_size", "fp_decode_rows",
                          "fp_plan_create", "fp_plan_create_config", "fp_decode_batch", "fp_plan_sync_status",
                          "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info", "fp_serve_create",
                          "fp_serve_dict_put", "fp_serve_submit", "fp_serve_poll", "fp_serve_release",
@@ -131,7 +140,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("config", ctypes.c_uint32), ("n_configs", ctypes.c_uint32),
                 ("slots_per_thread", ctypes.c_uint32 * 3), ("threads", ctypes.c_uint32),
                 ("grid", ctypes.c_uint32), ("index_blocks", ctypes.c_uint32), ("from_cache", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("total_tiles", ctypes.c_uint64), ("layout_bytes", ctypes.c_uint64),
+                ("slots_per_thread_fsst12", ctypes.c_uint32), ("total_tiles", ctypes.c_uint64),
+                ("layout_bytes", ctypes.c_uint64),
                 ("tune_ms", ctypes.c_float * 8)]
 
 
@@ -184,6 +194,15 @@ class Dict:
         if self._h is None:
             raise ValueError("dictionary was freed")
         return self._h
+
+    @property
+    def width(self) -> int:
+        """Dictionary read width fp_decode uses (8: split read, 16: whole entries)."""
+        return lib().fp_dict_width(self.handle)
+
+    def set_width(self, width: int, check: bool = True) -> int:
+        st = lib().fp_dict_set_width(self.handle, int(width))
+        return _check(st, "fp_dict_set_width") if check else st
 
     def free(self):
         if self._h is not None and _lib is not None:
@@ -308,6 +327,31 @@ def sync_status(stream=None) -> int:
     return lib().fp_sync_status(_stream(stream))
 
 
+def rows_size(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+              row_ids_ptr: int, n_rows: int, stream=None):
+    """fp_rows_size: (status, selected code slots, decoded bytes) of the
+    rows row_ids[0 .. n_rows).  Synchronous."""
+    slots, nbytes = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = lib().fp_rows_size(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, row_ids_ptr,
+                            n_rows, _stream(stream), ctypes.byref(slots), ctypes.byref(nbytes))
+    return st, int(slots.value), int(nbytes.value)
+
+
+def decode_rows(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                row_ids_ptr: int, n_rows: int, selected_slots: int, out_ptr: int, capacity: int, out_offsets_ptr: int,
+                stream=None, check: bool = True) -> int:
+    """fp_decode_rows: decode the strings row_ids[0 .. n_rows) in that order."""
+    st = lib().fp_decode_rows(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, row_ids_ptr,
+                              n_rows, selected_slots, out_ptr, capacity, out_offsets_ptr, _stream(stream))
+    return _check(st, "fp_decode_rows") if check else st
+
+
+def debug_stall_next(spin_limit: int, stream=None) -> int:
+    """fp_debug_stall_next: the next decode on ``stream`` gives up a
+    look-back after ``spin_limit`` polls (failure-detection test hook)."""
+    return lib().fp_debug_stall_next(_stream(stream), int(spin_limit))
+
+
 def variant_count(codec: int) -> int:
     return lib().fp_variant_count(codec)
 
@@ -329,8 +373,28 @@ def variant_selected(codec: int) -> int:
 
 
 def variant_for(codec: int, codes_bytes: int) -> int:
-    """The variant fp_decode uses for a code buffer of codes_bytes bytes."""
+    """The variant fp_decode uses for a code buffer of codes_bytes bytes
+    (with a dictionary of read width 8)."""
     return lib().fp_variant_for(codec, codes_bytes)
+
+
+def variant_for_dict(d: Dict, codes_bytes: int) -> int:
+    """The variant fp_decode uses with dictionary ``d`` for a code buffer of
+    codes_bytes bytes."""
+    return lib().fp_variant_for_dict(d.handle, codes_bytes)
+
+
+def variant_width(codec: int, v: int) -> int:
+    return lib().fp_variant_width(codec, v)
+
+
+def width_for_histogram(hist) -> int:
+    """The paper's split-read rule on a token-length histogram (17 counts,
+    lengths 0..16): 16 when more than 60 % of the tokens exceed 8 bytes."""
+    h = np.zeros(17, np.uint64)
+    a = np.asarray(hist, np.uint64)
+    h[:min(17, a.size)] = a[:17]
+    return lib().fp_width_for_histogram(h.ctypes.data)
 
 
 # ---- torch conveniences (tensors are only carriers of device memory) -------
@@ -404,6 +468,7 @@ class Plan:
         pi = PlanInfo()
         _check(lib().fp_plan_info(self.handle, ctypes.byref(pi)), "fp_plan_info")
         return {"config": pi.config, "n_configs": pi.n_configs, "slots_per_thread": list(pi.slots_per_thread),
+                "slots_per_thread_fsst12": pi.slots_per_thread_fsst12,
                 "threads": pi.threads, "grid": pi.grid, "index_blocks": pi.index_blocks,
                 "from_cache": bool(pi.from_cache), "total_tiles": pi.total_tiles, "layout_bytes": pi.layout_bytes,
                 "tune_ms": [round(float(x), 4) for x in list(pi.tune_ms)[:pi.n_configs]]}

@@ -36,7 +36,7 @@ fp_status cuda_fail(cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
-bool valid_codec(int c) { return c == FP_ONPAIR16 || c == FP_ONPAIR12 || c == FP_FSST8; }
+bool valid_codec(int c) { return c == FP_ONPAIR16 || c == FP_ONPAIR12 || c == FP_FSST8 || c == FP_FSST12; }
 
 namespace {
 
@@ -109,12 +109,13 @@ Workspace* find_workspace(cudaStream_t stream) {
 }
 
 // ---- variants and occupancy ----------------------------------------------------
-std::atomic<int> g_selected[4] = {{-1}, {-1}, {-1}, {-1}};
+std::atomic<int> g_selected[5] = {{-1}, {-1}, {-1}, {-1}, {-1}};
 
-// The selected variant, else the default for a code buffer of max_slots.
-int selected_variant(int codec, uint64_t max_slots) {
+// The selected variant, else the default for a code buffer of max_slots and
+// a dictionary read width.
+int selected_variant(int codec, uint64_t max_slots, int width) {
     const int v = g_selected[codec].load();
-    return v >= 0 ? v : variant_default(codec, max_slots);
+    return v >= 0 ? v : variant_default(codec, max_slots, width);
 }
 
 struct DevInfo {
@@ -176,6 +177,8 @@ fp_status check_common(fp_codec codec, const fp_dict* dict, const void* d_codes,
 
 fp_status status_from_bits(uint32_t bits) {
     if (bits & ERRB_TIMEOUT) return fail(FP_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (bits & ERRB_MISMATCH)
+        return fail(FP_ERR_INTERNAL, "decoder self-check: a warp tile's byte total disagrees with the scanned offsets");
     if (bits & ERRB_CORRUPT) return fail(FP_ERR_CORRUPT, "corrupt input (code >= n_entries, dangling escape or bad code_offsets)");
     if (bits & ERRB_CAPACITY) return fail(FP_ERR_CAPACITY, "decoded size exceeds out_capacity");
     if (bits & ERRB_OVERFLOW) return fail(FP_ERR_OVERFLOW, "decoded size exceeds 2^31-1");
@@ -184,6 +187,7 @@ fp_status status_from_bits(uint32_t bits) {
 
 fp_status status_code(uint32_t bits) {
     if (bits & ERRB_TIMEOUT) return FP_ERR_TIMEOUT;
+    if (bits & ERRB_MISMATCH) return FP_ERR_INTERNAL;
     if (bits & ERRB_CORRUPT) return FP_ERR_CORRUPT;
     if (bits & ERRB_CAPACITY) return FP_ERR_CAPACITY;
     if (bits & ERRB_OVERFLOW) return FP_ERR_OVERFLOW;
@@ -213,7 +217,7 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
                      uint64_t out_capacity, uint32_t* d_out_offsets, cudaStream_t stream, bool size_only,
                      Workspace** ws_out) {
     const uint64_t max_slots = max_slots_of(codec, codes_bytes);
-    const Variant* var = variant_get(codec, selected_variant(codec, max_slots));
+    const Variant* var = variant_get(codec, selected_variant(codec, max_slots, dict->width));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
     const uint64_t tile = variant_tile(*var);
@@ -245,6 +249,71 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
     const uint64_t grid = (n_tiles < (uint64_t)per_wave && !var->warp_tiles) ? n_tiles : (uint64_t)per_wave;
     cudaError_t e = launch_decode(codec, *var, p, static_cast<char*>(w->d_mem) + kWsHeaderBytes, max_slots,
                                   (int)grid, sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    if (ws_out) *ws_out = w;
+    return FP_OK;
+}
+
+// ---- selective decode --------------------------------------------------------
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+fp_status check_rows(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                     const uint32_t* d_code_offsets, uint32_t n_strings, const uint32_t* d_row_ids, uint32_t n_rows,
+                     uint8_t* d_out_bytes, uint64_t out_capacity, uint32_t* d_out_offsets, bool need_out) {
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, d_out_bytes, out_capacity,
+                                d_out_offsets, need_out);
+    if (st != FP_OK) return st;
+    if (n_strings == 0xffffffffu || n_rows == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings/n_rows must be below 2^32-1");
+    if (n_rows && !d_row_ids) return fail(FP_ERR_ARG, "d_row_ids is NULL");
+    if (reinterpret_cast<uintptr_t>(d_row_ids) % 4) return fail(FP_ERR_ARG, "d_row_ids not 4-byte aligned");
+    return FP_OK;
+}
+
+// Enqueue a selective decode of at most `slots` selected code slots: row
+// scan, gather, then the decode's launches on the gathered stream.
+fp_status run_rows(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                   const uint32_t* d_code_offsets, uint32_t n_strings, const uint32_t* d_row_ids, uint32_t n_rows,
+                   uint64_t slots, uint8_t* d_out_bytes, uint64_t out_capacity, uint32_t* d_out_offsets,
+                   cudaStream_t stream, bool size_only, Workspace** ws_out) {
+    if (slots > 0xffffffffull) return fail(FP_ERR_ARG, "selected_slots %llu: at most 2^32-1", (unsigned long long)slots);
+    const RowsLayout RL = rows_layout(codec, n_rows, slots);
+    const uint64_t dec_slots = max_slots_of(codec, RL.codes_bytes);
+    const Variant* var = variant_get(codec, selected_variant(codec, dec_slots, dict->width));
+    if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
+    int per_wave = 0, sms = 0;
+    fp_status st = grid_for(*var, &per_wave, &sms);
+    if (st != FP_OK) return st;
+    const size_t dec_bytes = al256(variant_scratch_bytes(*var, dec_slots));
+    Workspace* w = nullptr;
+    st = get_workspace(stream, dec_bytes + RL.bytes, 0, &w);
+    if (st != FP_OK) return st;
+    if ((++w->launches & ((1ull << 25) - 1)) == 0) {
+        cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(w->d_mem) + kWsHeaderBytes, 0, w->scratch_cap,
+                                        stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    char* scratch = static_cast<char*>(w->d_mem) + kWsHeaderBytes;
+    char* rows = scratch + dec_bytes;
+    WsHeader* ws = static_cast<WsHeader*>(w->d_mem);
+    const RowsArgs a{static_cast<const uint8_t*>(d_codes), max_slots_of(codec, codes_bytes), d_code_offsets,
+                     n_strings, d_row_ids, n_rows};
+    cudaError_t e = launch_rows_gather(codec, a, slots, true, rows, RL, ws, sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "row gather launch");
+    DecodeParams p;
+    p.dict = dict->view();
+    p.codes = reinterpret_cast<const uint8_t*>(rows + RL.o_codes);
+    p.codes_bytes = RL.codes_bytes;
+    p.max_slots = dec_slots;
+    p.code_offsets = reinterpret_cast<const uint32_t*>(rows + RL.o_v);
+    p.n_strings = n_rows;
+    p.out = d_out_bytes;
+    p.capacity = size_only ? 0 : out_capacity;
+    p.out_offsets = d_out_offsets;
+    p.ws = ws;
+    p.size_only = size_only ? 1 : 0;
+    const uint64_t n_tiles = dec_slots / variant_tile(*var) + 2;
+    const uint64_t grid = (n_tiles < (uint64_t)per_wave && !var->warp_tiles) ? n_tiles : (uint64_t)per_wave;
+    e = launch_decode(codec, *var, p, scratch, dec_slots, (int)grid, sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     if (ws_out) *ws_out = w;
     return FP_OK;
@@ -300,12 +369,30 @@ fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t*
     d->codec = codec;
     d->n_entries = n_entries;
     d->table_bytes = table.size();
+    // OnPair: the two 8-byte planes of the entries, and the read width by the
+    // paper's rule over the dictionary's own token lengths
+    std::vector<uint8_t> planes;
+    d->width = 8;
+    if (is_onpair(codec)) {
+        const size_t n_tab = table_entries(codec);
+        planes.resize(n_tab * 16);
+        for (size_t i = 0; i < n_tab; ++i) {
+            memcpy(&planes[i * 8], &table[i * 16], 8);
+            memcpy(&planes[(n_tab + i) * 8], &table[i * 16 + 8], 8);
+        }
+        uint64_t hist[17] = {0};
+        for (uint32_t i = 0; i < n_entries; ++i) hist[lens[i]] += 1;
+        d->width = width_for_histogram(hist);
+    }
     cudaError_t e = cudaGetDevice(&d->device);
     if (e == cudaSuccess) e = cudaMalloc(&d->d_table, table.size());
+    if (e == cudaSuccess && !planes.empty()) e = cudaMalloc(&d->d_planes, planes.size());
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->d_lens), lens.size());
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->d_bytes), nbytes ? nbytes : 1);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->d_offsets), offs.size() * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpyAsync(d->d_table, table.data(), table.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && !planes.empty())
+        e = cudaMemcpyAsync(d->d_planes, planes.data(), planes.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d->d_lens, lens.data(), lens.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && nbytes)
         e = cudaMemcpyAsync(d->d_bytes, h_bytes + base, nbytes, cudaMemcpyHostToDevice, stream);
@@ -328,12 +415,73 @@ fp_status fp_dict_free(fp_dict* d) {
     cudaDeviceSynchronize();
     cudaFree(d->d_table);
     cudaFree(d->d_lens);
+    if (d->d_planes) cudaFree(d->d_planes);
     cudaFree(d->d_bytes);
     cudaFree(d->d_offsets);
     cudaSetDevice(prev);
     delete d;
     return FP_OK;
 }
+
+fp_status fp_rows_size(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                       const uint32_t* d_code_offsets, uint32_t n_strings, const uint32_t* d_row_ids,
+                       uint32_t n_rows, fp_stream_t stream_, uint64_t* h_slots, uint64_t* h_bytes) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!h_slots || !h_bytes) return fail(FP_ERR_ARG, "h_slots/h_bytes is NULL");
+    fp_status st = check_rows(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_row_ids, n_rows,
+                              nullptr, 0, nullptr, false);
+    if (st != FP_OK) return st;
+    // 1: the selected rows' slot count (row scan alone)
+    const RowsLayout RL0 = rows_layout(codec, n_rows, 0);
+    Workspace* w = nullptr;
+    st = get_workspace(stream, RL0.bytes, 0, &w);
+    if (st != FP_OK) return st;
+    int dev_sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dict->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const RowsArgs a{static_cast<const uint8_t*>(d_codes), max_slots_of(codec, codes_bytes), d_code_offsets,
+                     n_strings, d_row_ids, n_rows};
+    e = launch_rows_gather(codec, a, ~0ull, false, static_cast<char*>(w->d_mem) + kWsHeaderBytes, RL0,
+                           static_cast<WsHeader*>(w->d_mem), dev_sms, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "row scan");
+    WsHeader h;
+    e = cudaMemcpy(&h, w->d_mem, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(row scan)");
+    *h_slots = h.rows_slots;
+    *h_bytes = 0;
+    if (h.status) return take_status(w, nullptr, stream);
+    // 2: gather and size the selected rows
+    st = run_rows(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_row_ids, n_rows, h.rows_slots,
+                  nullptr, 0, nullptr, stream, true, &w);
+    if (st != FP_OK) return st;
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return take_status(w, h_bytes, stream);
+}
+
+fp_status fp_decode_rows(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                         const uint32_t* d_code_offsets, uint32_t n_strings, const uint32_t* d_row_ids,
+                         uint32_t n_rows, uint64_t selected_slots, uint8_t* d_out_bytes, uint64_t out_capacity,
+                         uint32_t* d_out_offsets, fp_stream_t stream) {
+    fp_status st = check_rows(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_row_ids, n_rows,
+                              d_out_bytes, out_capacity, d_out_offsets, true);
+    if (st != FP_OK) return st;
+    return run_rows(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_row_ids, n_rows, selected_slots,
+                    d_out_bytes, out_capacity, d_out_offsets, reinterpret_cast<cudaStream_t>(stream), false, nullptr);
+}
+
+int fp_width_for_histogram(const uint64_t* hist17) { return hist17 ? width_for_histogram(hist17) : 8; }
+
+fp_status fp_dict_set_width(fp_dict* dict, int width) {
+    if (!dict) return fail(FP_ERR_ARG, "dict is NULL");
+    if (width != 8 && width != 16) return fail(FP_ERR_ARG, "width %d: must be 8 or 16", width);
+    if (width == 16 && !is_onpair(dict->codec)) return fail(FP_ERR_ARG, "FSST dictionaries have 8-byte entries");
+    dict->width = width;
+    return FP_OK;
+}
+
+int fp_dict_width(const fp_dict* dict) { return dict ? dict->width : 0; }
 
 fp_status fp_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
                     const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
@@ -399,6 +547,25 @@ fp_status fp_sync_status(fp_stream_t stream_) {
     return take_status(w, nullptr, stream);
 }
 
+fp_status fp_debug_stall_next(fp_stream_t stream_, uint32_t spin_limit) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (spin_limit < 1 || spin_limit > (1u << 20)) return fail(FP_ERR_ARG, "spin_limit %u outside 1..2^20", spin_limit);
+    Workspace* w = find_workspace(stream);
+    if (!w || !w->d_mem) return fail(FP_ERR_ARG, "no workspace on this stream yet (decode once first)");
+    // ticket 0 is taken here, so no launch ever publishes the first look-back
+    // word; the kernels reset both fields when the launch ends
+    // (pageable sources: each copy is staged before cudaMemcpyAsync returns)
+    const unsigned skip_first = 1u, limit = spin_limit;
+    char* h = static_cast<char*>(w->d_mem);
+    cudaError_t e = cudaMemcpyAsync(h + offsetof(WsHeader, tile_counter), &skip_first, sizeof(unsigned),
+                                    cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + offsetof(WsHeader, spin_limit), &limit, sizeof(unsigned), cudaMemcpyHostToDevice,
+                            stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(stall)");
+    return FP_OK;
+}
+
 int fp_variant_count(fp_codec codec) { return valid_codec(codec) ? variant_count(codec) : 0; }
 
 fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* slots_per_thread,
@@ -420,10 +587,21 @@ fp_status fp_variant_select(fp_codec codec, int v) {
     return FP_OK;
 }
 
-int fp_variant_selected(fp_codec codec) { return valid_codec(codec) ? selected_variant(codec, 1ull << 32) : -1; }
+int fp_variant_selected(fp_codec codec) { return valid_codec(codec) ? selected_variant(codec, 1ull << 32, 8) : -1; }
 
 int fp_variant_for(fp_codec codec, uint64_t codes_bytes) {
-    return valid_codec(codec) ? selected_variant(codec, max_slots_of(codec, codes_bytes)) : -1;
+    return valid_codec(codec) ? selected_variant(codec, max_slots_of(codec, codes_bytes), 8) : -1;
+}
+
+int fp_variant_for_dict(const fp_dict* dict, uint64_t codes_bytes) {
+    return dict && valid_codec(dict->codec)
+               ? selected_variant(dict->codec, max_slots_of(dict->codec, codes_bytes), dict->width)
+               : -1;
+}
+
+int fp_variant_width(fp_codec codec, int v) {
+    const Variant* var = valid_codec(codec) ? variant_get(codec, v) : nullptr;
+    return var ? var->width : 0;
 }
 
 }  // extern "C"
@@ -495,7 +673,7 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     // per 4,096-slot tile) covers far larger inputs than warp tiles' (20 bytes
     // per 512-slot tile).
     const int sel = g_selected[codec].load();
-    const Variant* var = variant_get(codec, sel >= 0 ? sel : (codec == FP_FSST8 ? 1 : 0));
+    const Variant* var = variant_get(codec, sel >= 0 ? sel : noalloc_default(codec));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     const uint64_t tile = variant_tile(*var);
     const uint64_t n_tiles = max_slots / tile + 2;
@@ -522,7 +700,12 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
     if (st != FP_OK) return st;
     char* base = static_cast<char*>(nd->ptr);
     cudaError_t e;
-    if ((++nd->launches & ((1ull << 25) - 1)) == 0) {
+    uint64_t launch_no;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);   // callers on several host threads share the count
+        launch_no = ++nd->launches;
+    }
+    if ((launch_no & ((1ull << 25) - 1)) == 0) {
         // tile status words carry a 26-bit launch tag; clear them well before it wraps
         e = cudaMemsetAsync(base + kWsHeaderBytes, 0, room, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");

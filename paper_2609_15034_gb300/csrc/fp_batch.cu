@@ -43,8 +43,8 @@ struct IdxBlock {
 
 struct IdxParams {
     const IdxBlock* blocks;
-    SlotSrc* src[3];
-    u32 tile[3];
+    SlotSrc* src[kQueues];
+    u32 tile[kQueues];
 };
 
 // Index pass of a batch: each block handles up to kIdxPerBlock boundaries of
@@ -71,14 +71,12 @@ template <int K16, int K12, int K8, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams bp) {
     const u32 epoch = *(volatile u32*)&bp.ws->epoch;
     const int q0 = blockIdx.x < bp.split[0] ? 0 : (blockIdx.x < bp.split[1] ? 1 : 2);
-    bool reinit = false;
-    for (int i = 0; i < 3; ++i) {
-        const int q = (q0 + i) % 3;
+    for (int i = 0; i < kBlockQueues; ++i) {
+        const int q = (q0 + i) % kBlockQueues;
         if (bp.q[q].n_tiles == 0) continue;
-        if (q == 0) Decoder<FP_ONPAIR16, K16, false, MINB, true>::run_queue(bp, 0, epoch, reinit);
-        else if (q == 1) Decoder<FP_ONPAIR12, K12, false, MINB, true>::run_queue(bp, 1, epoch, reinit);
-        else Decoder<FP_FSST8, K8, false, MINB, true>::run_queue(bp, 2, epoch, reinit);
-        reinit = true;
+        if (q == 0) Decoder<FP_ONPAIR16, K16, false, MINB, true>::run_queue(bp, 0, epoch);
+        else if (q == 1) Decoder<FP_ONPAIR12, K12, false, MINB, true>::run_queue(bp, 1, epoch);
+        else Decoder<FP_FSST8, K8, false, MINB, true>::run_queue(bp, 2, epoch);
     }
     finish_launch(bp.ws, epoch);
 }
@@ -141,18 +139,20 @@ __device__ __forceinline__ void reduce_queue(const BatchParams& bp, int q, u64 t
 
 template <int K16, int K12, int K8>
 __global__ void __launch_bounds__(256, 3) wbatch_reduce_kernel(const BatchParams bp) {
+    // FSST-12 chunks run with the OnPair-12 slots per lane (both 12-bit codes)
     // Every block takes a contiguous range of each queue's tiles (its warps
     // interleaved inside it), so a block's warps mostly work in one chunk and
     // that chunk's length table stays in the SM's L1 (12 % faster than tiles
     // interleaved over the whole grid on the mixed 4,096-chunk batch).
     const u64 b = blockIdx.x, B = gridDim.x, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
         const u64 n = bp.q[q].n_tiles;
         const u64 lo = n * b / B, hi = n * (b + 1) / B;
         if (q == 0) reduce_queue<FP_ONPAIR16, K16>(bp, 0, lo + w, hi, 8);
         else if (q == 1) reduce_queue<FP_ONPAIR12, K12>(bp, 1, lo + w, hi, 8);
-        else reduce_queue<FP_FSST8, K8>(bp, 2, lo + w, hi, 8);
+        else if (q == 2) reduce_queue<FP_FSST8, K8>(bp, 2, lo + w, hi, 8);
+        else reduce_queue<FP_FSST12, K12>(bp, 3, lo + w, hi, 8);
     }
 }
 
@@ -217,7 +217,7 @@ __device__ __forceinline__ void decode_queue(const BatchParams& bp, int q, u64 t
         // the error word's address is read before the tile: once the tile's
         // last __syncwarp() has passed, other lanes may overwrite the record
         unsigned* const err_word = rs.p.err_word;
-        C::decode_tile(rs.p, rs.x, t - rs.tile_base, cur, nullptr, rs.p.dict.lens, area, err);
+        C::decode_tile(rs.p, rs.x, t - rs.tile_base, cur, bp.ex + rs.wt_base, nullptr, rs.p.dict.lens, area, err);
         if (err) atomicOr(err_word, err);
         cur = nxt;
         rc = rn;
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) wbatch_decode_kernel(const Batc
     decode_queue<FP_ONPAIR16, K16>(bp, 0, gw, bp.q[0].n_tiles, W, mine, rs);
     decode_queue<FP_ONPAIR12, K12>(bp, 1, gw, bp.q[1].n_tiles, W, mine, rs);
     decode_queue<FP_FSST8, K8>(bp, 2, gw, bp.q[2].n_tiles, W, mine, rs);
+    decode_queue<FP_FSST12, K12>(bp, 3, gw, bp.q[3].n_tiles, W, mine, rs);
 }
 
 template <int K16, int K12, int K8, int NW>
@@ -264,7 +265,7 @@ constexpr size_t wbatch_smem() {
 }
 
 struct BatchKernel {
-    int k[3];            // code slots per thread: OnPair-16, OnPair-12, FSST-8
+    int k[kQueues];      // code slots per thread: OnPair-16, OnPair-12, FSST-8, FSST-12 (0: not served)
     int minb;            // blocks per SM the registers are budgeted for
     size_t smem_bytes;   // max over the three pipelines
     const void* kernel;  // the decode kernel
@@ -280,7 +281,7 @@ BatchKernel make_batch_kernel() {
     const size_t b = sizeof(typename Decoder<FP_ONPAIR12, K12, false, MINB, true>::S);
     const size_t c = sizeof(typename Decoder<FP_FSST8, K8, false, MINB, true>::S);
     BatchKernel k{};
-    k.k[0] = K16; k.k[1] = K12; k.k[2] = K8;
+    k.k[0] = K16; k.k[1] = K12; k.k[2] = K8; k.k[3] = 0;   // no FSST-12 block pipeline
     k.minb = MINB;
     k.smem_bytes = std::max(a, std::max(b, c));
     k.kernel = (const void*)&batch_kernel<K16, K12, K8, MINB>;
@@ -292,7 +293,7 @@ BatchKernel make_batch_kernel() {
 template <int K16, int K12, int K8, int NW, int MINB>
 BatchKernel make_wbatch_kernel() {
     BatchKernel k{};
-    k.k[0] = K16; k.k[1] = K12; k.k[2] = K8;
+    k.k[0] = K16; k.k[1] = K12; k.k[2] = K8; k.k[3] = K12;
     k.minb = MINB;
     k.smem_bytes = wbatch_smem<K16, K12, K8, NW>();
     k.kernel = (const void*)&wbatch_decode_kernel<K16, K12, K8, NW, MINB>;
@@ -366,13 +367,13 @@ namespace {
 // writes the fourth and the look-back words are tagged per launch.
 struct LayoutImage {
     std::vector<char> bytes;
-    size_t o_src[3], o_tc[3], o_ib, o_sb, o_first, o_ts, o_agg, o_ex, table_bytes, total_bytes;
+    size_t o_src[kQueues], o_tc[kQueues], o_ib, o_sb, o_first, o_ts, o_agg, o_ex, table_bytes, total_bytes;
     uint64_t total_tiles = 0;
     uint64_t status_words = 0;   // look-back words (per tile, or per tile-scan block with warp tiles)
     uint32_t n_idx = 0;
     uint32_t n_sb = 0;           // tile-scan blocks (warp tiles)
-    uint32_t n_tiles_q[3], n_chunks_q[3];
-    uint64_t slots_q[3];
+    uint32_t n_tiles_q[kQueues], n_chunks_q[kQueues];
+    uint64_t slots_q[kQueues];
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -382,14 +383,16 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // offsets until relocate() adds the layout's base.
 fp_status make_layout(const fp_chunk* chunks, uint32_t n, const BatchKernel& BK, uint32_t* d_status,
                       unsigned long long* d_total, WsHeader* ws, LayoutImage& L) {
-    std::vector<uint32_t> qlist[3];
+    std::vector<uint32_t> qlist[kQueues];
     for (uint32_t i = 0; i < n; ++i) qlist[chunks[i].codec - 1].push_back(i);
-    std::vector<SlotSrc> src[3];
-    std::vector<uint32_t> tchunk[3];
+    if (!qlist[3].empty() && BK.k[3] == 0)
+        return fail(FP_ERR_ARG, "FSST-12 chunks need a warp-tile batch configuration");
+    std::vector<SlotSrc> src[kQueues];
+    std::vector<uint32_t> tchunk[kQueues];
     std::vector<IdxBlock> iblk;
     std::vector<uint2> sblk;
     uint64_t tile_glob = 0, first_glob = 0, sb_glob = 0;
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
         const int codec = q + 1;
         const uint64_t T = (uint64_t)(BK.warp_tiles ? 32 : kWork) * (uint64_t)BK.k[q];
         uint32_t tile_q = 0;
@@ -444,8 +447,8 @@ fp_status make_layout(const fp_chunk* chunks, uint32_t n, const BatchKernel& BK,
     }
     if (iblk.size() > 0x7fffffffull) return fail(FP_ERR_ARG, "batch has too many strings");
     size_t off = 0;
-    for (int q = 0; q < 3; ++q) { L.o_src[q] = off; off = align256(off + src[q].size() * sizeof(SlotSrc)); }
-    for (int q = 0; q < 3; ++q) { L.o_tc[q] = off; off = align256(off + tchunk[q].size() * sizeof(uint32_t)); }
+    for (int q = 0; q < kQueues; ++q) { L.o_src[q] = off; off = align256(off + src[q].size() * sizeof(SlotSrc)); }
+    for (int q = 0; q < kQueues; ++q) { L.o_tc[q] = off; off = align256(off + tchunk[q].size() * sizeof(uint32_t)); }
     L.o_ib = off; off = align256(off + iblk.size() * sizeof(IdxBlock));
     L.o_sb = off; off = align256(off + sblk.size() * sizeof(uint2));
     L.table_bytes = off;
@@ -459,7 +462,7 @@ fp_status make_layout(const fp_chunk* chunks, uint32_t n, const BatchKernel& BK,
     L.n_idx = (uint32_t)iblk.size();
     L.n_sb = (uint32_t)sblk.size();
     L.bytes.assign(L.table_bytes, 0);
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
         if (!src[q].empty()) memcpy(&L.bytes[L.o_src[q]], src[q].data(), src[q].size() * sizeof(SlotSrc));
         if (!tchunk[q].empty()) memcpy(&L.bytes[L.o_tc[q]], tchunk[q].data(), tchunk[q].size() * sizeof(uint32_t));
     }
@@ -470,7 +473,7 @@ fp_status make_layout(const fp_chunk* chunks, uint32_t n, const BatchKernel& BK,
 
 // Turn the records' offsets into addresses of a layout placed at `base`.
 void relocate(LayoutImage& L, char* base) {
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
         SlotSrc* s = reinterpret_cast<SlotSrc*>(&L.bytes[L.o_src[q]]);
         for (uint32_t c = 0; c < L.n_chunks_q[q]; ++c) {
             s[c].p.tile_status = reinterpret_cast<unsigned long long*>(base + L.o_ts) + (uintptr_t)s[c].p.tile_status;
@@ -494,7 +497,7 @@ fp_status launch_shape(const LayoutImage& L, const BatchKernel& BK, int bps_limi
     const uint64_t per_block = BK.warp_tiles ? (uint64_t)(BK.threads / 32) : 1;   // tiles a block takes at once
     if (grid > (L.total_tiles + per_block - 1) / per_block) grid = (L.total_tiles + per_block - 1) / per_block;
     if (grid < 1) grid = 1;
-    const double tot = (double)(L.slots_q[0] + L.slots_q[1] + L.slots_q[2]) + 1e-9;
+    const double tot = (double)(L.slots_q[0] + L.slots_q[1] + L.slots_q[2]) + 1e-9;   // block-pipeline queues
     uint32_t g[3];
     for (int q = 0; q < 3; ++q) {
         g[q] = L.n_tiles_q[q] ? (uint32_t)std::floor((double)grid * (double)L.slots_q[q] / tot) : 0u;
@@ -516,7 +519,7 @@ void make_params(const LayoutImage& L, const BatchKernel& BK, char* base, WsHead
                  BatchParams& bp, IdxParams& ip) {
     memset(&bp, 0, sizeof(bp));
     bp.ws = ws;
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
         bp.q[q].src = reinterpret_cast<const SlotSrc*>(base + L.o_src[q]);
         bp.q[q].tile_chunk = reinterpret_cast<const uint32_t*>(base + L.o_tc[q]);
         bp.q[q].n_tiles = L.n_tiles_q[q];
@@ -532,9 +535,9 @@ void make_params(const LayoutImage& L, const BatchKernel& BK, char* base, WsHead
     }
     memset(&ip, 0, sizeof(ip));
     ip.blocks = reinterpret_cast<const IdxBlock*>(base + L.o_ib);
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
         ip.src[q] = reinterpret_cast<SlotSrc*>(base + L.o_src[q]);
-        ip.tile[q] = (u32)((BK.warp_tiles ? 32 : kWork) * BK.k[q]);
+        ip.tile[q] = (u32)((BK.warp_tiles ? 32 : kWork) * (BK.k[q] ? BK.k[q] : 16));
     }
 }
 
@@ -703,7 +706,10 @@ fp_status plan_create(const fp_chunk* chunks, uint32_t n, int force_cfg, const c
         e = cudaEventCreate(&a);
         if (e == cudaSuccess) e = cudaEventCreate(&b);
         float best = 0.0f;
+        bool has_fsst12 = false;
+        for (const fp_chunk& c : P->chunks) has_fsst12 |= c.codec == FP_FSST12;
         for (int c = 0; c < (int)configs().size() && e == cudaSuccess && st == FP_OK; ++c) {
+            if (has_fsst12 && batch_kernels()[configs()[c].kernel].k[3] == 0) continue;   // no FSST-12 queue
             st = build_layout(P, c);
             if (st != FP_OK) break;
             e = launch_batch(P, stream);
@@ -954,6 +960,7 @@ fp_status fp_plan_info(const fp_plan* plan, fp_plan_info_t* info) {
     memset(info, 0, sizeof(*info));
     info->config = (uint32_t)plan->config;
     for (int q = 0; q < 3; ++q) info->slots_per_thread[q] = (uint32_t)BK.k[q];
+    info->slots_per_thread_fsst12 = (uint32_t)BK.k[3];
     info->threads = (uint32_t)BK.threads;
     info->grid = (uint32_t)plan->grid;
     info->total_tiles = plan->total_tiles;

@@ -1,8 +1,8 @@
-// Single-column decoder for sm_103a: the kernel instantiations of the block
-// pipeline (fp_decoder.cuh) and of the warp-tile decoder (fp_warp.cuh), the
-// variant table with its size-dependent defaults, and the launches of one
-// decode call (index pass + block-pipeline decode, or index pass and reduce
-// in one grid + tile scan + warp-tile decode).
+// Single-column decoder for sm_103a: the variant tables (their kernel
+// instantiations are in fp_var*.cu) with their size- and width-dependent
+// defaults, and the launches of one decode call (index pass + block-pipeline
+// decode, or index pass and reduce in one grid + tile scan + warp-tile
+// decode).
 #include "fp_decoder.cuh"
 #include "fp_warp.cuh"
 
@@ -17,73 +17,20 @@ __global__ void __launch_bounds__(256) index_kernel(const DecodeParams p, u32 ti
                  (u64)blockIdx.x * blockDim.x + threadIdx.x, (u64)gridDim.x * blockDim.x, first);
 }
 
-template <int CODEC, int K, bool DSMEM, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) decode_kernel(const DecodeParams p) {
-    Decoder<CODEC, K, DSMEM, MINB>::run(p);
-}
-
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// Variant tables
-// ---------------------------------------------------------------------------
-template <int CODEC, int K, bool DSMEM, int MINB>
-static Variant make_variant() {
-    typedef Decoder<CODEC, K, DSMEM, MINB> D;
-    Variant v{};
-    v.threads = kThreads;
-    v.slots_per_thread = K;
-    v.dict_smem = DSMEM ? 1 : 0;
-    v.smem_bytes = sizeof(typename D::S);
-    v.kernel = (const void*)&decode_kernel<CODEC, K, DSMEM, MINB>;
-    v.warp_tiles = 0;
-    return v;
-}
-
-template <int CODEC, int K, bool DSMEM, int NW, int MINB>
-static Variant make_warp_variant() {
-    typedef WarpCore<CODEC, K, DSMEM> C;
-    Variant v{};
-    v.threads = NW * 32;
-    v.slots_per_thread = K;
-    v.dict_smem = DSMEM ? 1 : 0;
-    v.smem_bytes = (size_t)C::DICT_BYTES + (DSMEM ? (size_t)C::LENS_BYTES : 0) + NW * sizeof(WarpArea<K>);
-    v.kernel = (const void*)&warp_decode_kernel<CODEC, K, DSMEM, NW, MINB>;
-    v.warp_tiles = 1;
-    v.reduce = (const void*)&reduce_kernel<CODEC, K, DSMEM>;
-    v.scan = (const void*)&tiles_scan_kernel<CODEC == FP_FSST8>;
-    return v;
-}
+// Variant tables (one translation unit per codec).
+const Variant* variants_onpair16(int* n);
+const Variant* variants_onpair12(int* n);
+const Variant* variants_fsst8(int* n);
+const Variant* variants_fsst12(int* n);
 
 static const Variant* table_for(int codec, int* n) {
-    static const Variant v16[] = {
-        make_variant<FP_ONPAIR16, 16, false, 2>(),
-        make_variant<FP_ONPAIR16, 8, false, 2>(),
-        make_warp_variant<FP_ONPAIR16, 16, false, 8, 3>(),
-        make_warp_variant<FP_ONPAIR16, 16, false, 8, 2>(),
-        make_warp_variant<FP_ONPAIR16, 16, false, 16, 1>(),
-    };
-    static const Variant v12[] = {
-        make_variant<FP_ONPAIR12, 16, true, 2>(),
-        make_variant<FP_ONPAIR12, 16, false, 2>(),
-        make_variant<FP_ONPAIR12, 8, true, 2>(),
-        make_warp_variant<FP_ONPAIR12, 16, true, 8, 2>(),
-        make_warp_variant<FP_ONPAIR12, 16, false, 8, 3>(),
-        make_warp_variant<FP_ONPAIR12, 16, true, 10, 2>(),
-        make_warp_variant<FP_ONPAIR12, 16, true, 16, 1>(),
-        make_warp_variant<FP_ONPAIR12, 16, false, 20, 1>(),
-    };
-    static const Variant v8[] = {
-        make_variant<FP_FSST8, 16, true, 2>(),
-        make_variant<FP_FSST8, 32, true, 2>(),
-        make_warp_variant<FP_FSST8, 16, true, 8, 3>(),
-        make_warp_variant<FP_FSST8, 32, true, 8, 2>(),
-        make_warp_variant<FP_FSST8, 32, true, 16, 1>(),
-    };
     switch (codec) {
-        case FP_ONPAIR16: *n = (int)(sizeof(v16) / sizeof(v16[0])); return v16;
-        case FP_ONPAIR12: *n = (int)(sizeof(v12) / sizeof(v12[0])); return v12;
-        case FP_FSST8: *n = (int)(sizeof(v8) / sizeof(v8[0])); return v8;
+        case FP_ONPAIR16: return variants_onpair16(n);
+        case FP_ONPAIR12: return variants_onpair12(n);
+        case FP_FSST8: return variants_fsst8(n);
+        case FP_FSST12: return variants_fsst12(n);
         default: *n = 0; return nullptr;
     }
 }
@@ -101,21 +48,34 @@ const Variant* variant_get(int codec, int v) {
 }
 
 // Defaults chosen by measurement on GB300 (synthetic columns, every variant
-// timed at 30k..10M strings): warp tiles for all three codecs, one block of
-// 16 warps per SM for large columns.  The one-block shapes run the same code
+// timed at 30k..10M strings): warp tiles for every codec, one block of 16
+// warps per SM for large columns.  The one-block shapes run the same code
 // with the same registers and warps per SM as two blocks of 8 warps, with one
 // copy of the dictionary per SM instead of two; they were faster for every
-// codec (10M strings: OnPair-12 1446 vs 1342
-// GB/s, FSST-8 963 vs 902, OnPair-16 1029 vs 990).  OnPair-12 below 2^23
-// slots reads the dictionary through L1 (20 warps; staging it per block does
-// not pay: 637 vs 613 GB/s at 300k strings); FSST-8 below 2^22 slots uses
-// 16-slot lanes.
-int variant_default(int codec, uint64_t max_slots) {
+// codec (10M strings: OnPair-12 1446 vs 1342 GB/s, FSST-8 963 vs 902,
+// OnPair-16 1029 vs 990).  OnPair-12 below 2^23 slots reads the dictionary
+// through L1 (20 warps; staging it per block does not pay: 637 vs 613 GB/s
+// at 300k strings); FSST-8 below 2^22 slots uses 16-slot lanes.  The OnPair
+// codecs come in both read widths (split read W = 8, whole entries W = 16);
+// the dictionary's width picks between them.
+int variant_default(int codec, uint64_t max_slots, int width) {
+    const bool split = width != 16;
     switch (codec) {
-        case FP_ONPAIR12: return max_slots >= (1ull << 23) ? 6 : 7;
-        case FP_ONPAIR16: return 4;
+        case FP_ONPAIR12:
+            if (max_slots >= (1ull << 23)) return split ? 6 : 8;
+            return split ? 9 : 7;
+        case FP_ONPAIR16: return split ? 5 : 4;
         case FP_FSST8: return max_slots >= (1ull << 22) ? 4 : 2;
+        case FP_FSST12: return max_slots >= (1ull << 23) ? 0 : 1;
         default: return 0;
+    }
+}
+
+int noalloc_default(int codec) {
+    switch (codec) {
+        case FP_FSST8: return 1;    // block pipeline, 32 slots per thread
+        case FP_FSST12: return 0;   // no block pipeline: warp tiles
+        default: return 0;          // block pipeline
     }
 }
 

@@ -62,7 +62,7 @@ constexpr u32 kBarExcl = 5;                   // + slot (3): scan warp -> worker
 constexpr u64 kFlagAgg = 1ull;
 constexpr u64 kFlagInc = 2ull;
 constexpr u64 kPayloadMask = (1ull << 36) - 1ull;
-constexpr u32 kSpinLimit = 1u << 21;   // ~2 s with the backoff below
+constexpr u32 kSpinLimit = 1u << 20;   // about a second with the backoff below
 
 // Named barriers in their non-aligned form (barrier.sync / barrier.arrive);
 // each call first reconverges its warp.
@@ -214,6 +214,8 @@ __device__ void lookback(const u64* status, long long tile, u32 epoch, WsHeader*
     Elem acc = elem_identity();
     long long base = tile - 1;
     u32 spins = 0;
+    const u32 lim = *(volatile u32*)&ws->spin_limit;
+    const u32 limit = lim ? lim : kSpinLimit;
     for (;;) {
         u64 w[V];
         u32 fl[V];
@@ -245,7 +247,7 @@ __device__ void lookback(const u64* status, long long tile, u32 epoch, WsHeader*
         }
         if (__any_sync(0xffffffffu, missing)) {
             bool give_up = false;
-            if (lane == 0) give_up = (++spins > kSpinLimit) || (*(volatile u32*)&ws->abort != 0u);
+            if (lane == 0) give_up = (++spins > limit) || (*(volatile u32*)&ws->abort != 0u);
             give_up = __shfl_sync(0xffffffffu, give_up, 0);
             if (give_up) {
                 if (lane == 0) {
@@ -548,7 +550,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, 
                  : "memory");
 }
 
-constexpr u64 kWaitLimitNs = 2000000000ull;   // bounded waits give up after 2 s
+// Bounded mbarrier waits give up after 4 s: well after any look-back has
+// given up (kSpinLimit), so a wait that a look-back holds up never expires
+// first.  The abort flag does not end them: once a look-back has given up
+// the pipeline still runs to its end (with wrong positions, every write in
+// bounds), so the workers, the scan warp and the producer keep seeing the
+// same ring state and every named barrier stays matched.
+constexpr u64 kWaitLimitNs = 4000000000ull;
 
 // Wait for a phase of `bar`; gives up (status ERRB_TIMEOUT, abort flag) after
 // kWaitLimitNs.  Returns false on giving up.
@@ -558,7 +566,7 @@ __device__ bool mbar_wait(u64* bar, u32 parity, WsHeader* ws) {
     for (u32 i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63u) == 63u) {
-            if (global_timer_ns() - t0 > kWaitLimitNs || *(volatile u32*)&ws->abort != 0u) {
+            if (global_timer_ns() - t0 > kWaitLimitNs) {
                 atomicOr(&ws->status, ERRB_TIMEOUT);
                 *(volatile u32*)&ws->abort = 1u;
                 return false;
@@ -681,6 +689,7 @@ __device__ __forceinline__ void finish_launch(WsHeader* ws, u32 epoch) {
             ws->queue_counter[2] = 0;
             ws->exit_counter = 0;
             ws->abort = 0;
+            ws->spin_limit = 0;
             u32 ne = (epoch + 1u) & kEpochMask;
             if (ne == 0u) ne = 1u;
             ws->epoch = ne;
@@ -1273,18 +1282,29 @@ struct Decoder {
     }
 
     // ---- block setup and the worker loop ------------------------------------
-    static __device__ __forceinline__ void init_ring(S& sm, bool reinit) {
+    static __device__ __forceinline__ void init_ring(S& sm) {
         if (threadIdx.x == 0) {
             for (int s = 0; s < kSlots; ++s) {
-                if (reinit) {
-                    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&sm.ring[s].full)) : "memory");
-                    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&sm.ring[s].req)) : "memory");
-                }
                 mbar_init(&sm.ring[s].full, 1u);
                 mbar_init(&sm.ring[s].req, 1u);
                 sm.ring[s].nready = 0u;
             }
             mbar_init_fence();
+        }
+    }
+    // The ring's mbarriers must be invalidated before their memory holds
+    // anything else: a batch block re-lays out its shared memory for every
+    // codec queue, and another queue's layout puts ordinary data (the
+    // per-thread byte counts of the offsets) where these barriers were.
+    // Writing over live mbarrier objects is undefined; it once showed as
+    // string offsets off by a few bytes, from the threads whose counts sat on
+    // the barriers.  Called by every thread after the queue's last barrier.
+    static __device__ __forceinline__ void inval_ring(S& sm) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < kSlots; ++s) {
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&sm.ring[s].full)) : "memory");
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&sm.ring[s].req)) : "memory");
+            }
         }
     }
 
@@ -1323,7 +1343,7 @@ struct Decoder {
             for (int i = threadIdx.x; i < LENS_BYTES / 16; i += kThreads)
                 sm.lens4[i] = __ldg(lsrc + i);
         }
-        init_ring(sm, false);
+        init_ring(sm);
         const u32 epoch = *(volatile u32*)&ws->epoch;
         const Extent x = column_extent(p, TILE);
         __syncthreads();
@@ -1342,12 +1362,14 @@ struct Decoder {
     }
 
     // ---- one codec queue of a batch -------------------------------------------
-    // Every thread of the block calls this; it returns with the ring idle.
-    static __device__ __forceinline__ void run_queue(const BatchParams& bp, int q, u32 epoch, bool reinit) {
+    // Every thread of the block calls this; it returns with the ring's
+    // barriers invalidated, so that the next queue may lay out the block's
+    // shared memory differently.
+    static __device__ __forceinline__ void run_queue(const BatchParams& bp, int q, u32 epoch) {
         extern __shared__ __align__(128) unsigned char smem_raw[];
         S& sm = *reinterpret_cast<S*>(smem_raw);
         WsHeader* ws = bp.ws;
-        init_ring(sm, reinit);
+        init_ring(sm);
         __syncthreads();
         const u32 warp = threadIdx.x >> 5;
         const SlotColumns cols{sm.src};
@@ -1359,6 +1381,7 @@ struct Decoder {
             work(cols, sm, epoch, ws);
         }
         __syncthreads();
+        inval_ring(sm);   // the next init_ring (same thread) follows it in program order
     }
 };
 

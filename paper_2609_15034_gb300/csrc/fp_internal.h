@@ -16,6 +16,9 @@ constexpr uint32_t ERRB_CORRUPT = 1u;
 constexpr uint32_t ERRB_CAPACITY = 2u;
 constexpr uint32_t ERRB_OVERFLOW = 4u;
 constexpr uint32_t ERRB_TIMEOUT = 8u;
+// A warp tile's byte total, recomputed by the decode, differs from the
+// offsets the tile scan (or a stored sidecar) gave its neighbour.
+constexpr uint32_t ERRB_MISMATCH = 16u;
 
 // Device workspace header (one per stream).  It is followed by the tile
 // status words of the single-pass prefix scan (one u64 per tile, at
@@ -25,11 +28,12 @@ struct WsHeader {
     unsigned int exit_counter;   // blocks that have finished
     unsigned int epoch;          // launch generation tag of tile status words
     unsigned int status;         // sticky ERRB_* bits
-    unsigned long long reserved;
+    unsigned long long rows_slots;   // selective decode: code slots of the selected rows
     unsigned long long total;    // decoded size of the last launch
     unsigned int abort;          // set when a bounded wait gave up
     unsigned int queue_counter[3];   // batched decode: next tile ticket of each codec queue
-    unsigned int pad[20];
+    unsigned int spin_limit;     // polls before a look-back gives up (0 = the built-in limit); reset per launch
+    unsigned int pad[19];
 };
 constexpr size_t kWsHeaderBytes = 128;
 static_assert(sizeof(WsHeader) == kWsHeaderBytes, "workspace header size");
@@ -39,8 +43,10 @@ constexpr unsigned kEpochMask = (1u << kEpochBits) - 1u;
 
 // Device view of a dictionary (passed by value to kernels).
 struct DictView {
-    const void* table;        // 2^w entries, 16 B (OnPair) or 8 B (FSST-8) each, zero padded
+    const void* table;        // 2^w entries, 16 B (OnPair) or 8 B (FSST-8, FSST-12) each, zero padded
     const uint8_t* lens;      // 2^w token lengths; 0 = no token (or the FSST-8 escape)
+    const void* planes;       // OnPair only: low plane (bytes 0-7 of each entry, 8 B stride),
+                              // then high plane (bytes 8-15), 2^w entries each; else null
     const uint8_t* bytes;     // interchange layout: concatenated token bytes
     const uint32_t* offsets;  // interchange layout: n_entries + 1 offsets (rebased to 0)
     uint32_t n_entries;
@@ -96,10 +102,17 @@ struct BatchQueue {
     uint32_t n_chunks;
 };
 
+// Codec queues of a batch: OnPair-16, OnPair-12, FSST-8, FSST-12 (queue =
+// codec - 1).  The block pipeline serves the first three; FSST-12 chunks
+// need a warp-tile configuration.
+constexpr int kQueues = 4;
+constexpr int kBlockQueues = 3;
+
 struct BatchParams {
     WsHeader* ws;
-    BatchQueue q[3];      // OnPair-16, OnPair-12, FSST-8
-    uint32_t split[2];    // blocks [0, split[0]) start on queue 0, [split[0], split[1]) on 1, the rest on 2
+    BatchQueue q[kQueues];
+    uint32_t split[2];    // block pipeline: blocks [0, split[0]) start on queue 0, [split[0], split[1]) on 1,
+                          // the rest on 2
     // warp-tile batches only
     unsigned long long* agg;        // scan element of every warp tile
     unsigned long long* ex;         // scanned offset | entering state of every warp tile
@@ -117,6 +130,8 @@ struct Variant {
     const void* kernel;   // the decode kernel
     int warp_tiles;       // 0: block pipeline (one launch after the index pass);
                           // 1: warp tiles (index pass + reduce, tile scan and warp decode launches)
+    int width;            // dictionary read width W: 16 = whole entry, 8 = split read (low plane,
+                          // high plane only for tokens longer than 8 bytes; paper Sec. 3.2)
     const void* reduce;   // warp tiles: the reduce kernel (its first blocks run the index pass)
     const void* scan;     // warp tiles: the tile scan kernel
 };
@@ -124,7 +139,12 @@ struct Variant {
 // Variant tables (fp_decode.cu).
 int variant_count(int codec);
 const Variant* variant_get(int codec, int v);
-int variant_default(int codec, uint64_t max_slots);   // default for a code buffer of max_slots slots
+// Default for a code buffer of max_slots slots and a dictionary read width
+// (8 or 16; only the OnPair codecs have both).
+int variant_default(int codec, uint64_t max_slots, int width);
+// The variant fp_decode_noalloc uses when none is selected: the block
+// pipeline where the codec has one (its scratch covers the largest inputs).
+int noalloc_default(int codec);
 
 // Launch helpers (fp_decode.cu, fp_plain.cu).
 uint64_t variant_tile(const Variant& v);   // code slots per tile (block tile or warp tile)
@@ -137,6 +157,30 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p, 
                           int grid, int sms, cudaStream_t stream);
 cudaError_t launch_plain(int codec, const DecodeParams& p, uint32_t* d_scratch, size_t scratch_words,
                          cudaStream_t stream);
+
+// Selective decode (fp_rows.cu): the selected rows of a column and where their
+// codes are gathered.
+struct RowsArgs {
+    const uint8_t* codes;          // the column's stored code buffer
+    uint64_t max_slots;            // whole slots in it
+    const uint32_t* code_offsets;  // n_strings + 1
+    uint32_t n_strings;
+    const uint32_t* row_ids;       // n_rows
+    uint32_t n_rows;
+};
+// Scratch of a selective decode (after the decode's own scratch): the
+// virtual code offsets v[0 .. n_rows], the scan's block sums, the gathered
+// stream (codes_bytes of it are handed to the decode).
+struct RowsLayout {
+    size_t o_v, o_sums, o_codes, bytes;
+    uint64_t codes_bytes;
+};
+RowsLayout rows_layout(int codec, uint32_t n_rows, uint64_t selected_slots);
+// Row lengths, their scan into v (ws->rows_slots gets the total; more than
+// selected_slots sets ERRB_CAPACITY) and, with `gather`, the gather of at
+// most selected_slots codes: three or four launches.
+cudaError_t launch_rows_gather(int codec, const RowsArgs& a, uint64_t selected_slots, bool gather, void* scratch,
+                               const RowsLayout& L, WsHeader* ws, int sms, cudaStream_t stream);
 size_t plain_scratch_words(uint32_t n_strings);
 
 // A launch slot for batches built on the fly (the server's waves): device
@@ -182,30 +226,46 @@ fp_status repack_dictionary(fp_codec codec, const uint8_t* h_bytes, const uint32
                             std::vector<uint8_t>& table, std::vector<uint8_t>& lens, std::vector<uint32_t>& offs);
 
 inline uint32_t code_bits(int codec) {
-    return codec == FP_ONPAIR16 ? 16u : codec == FP_ONPAIR12 ? 12u : codec == FP_FSST8 ? 8u : 0u;
+    return codec == FP_ONPAIR16 ? 16u : (codec == FP_ONPAIR12 || codec == FP_FSST12) ? 12u : codec == FP_FSST8 ? 8u : 0u;
 }
-inline uint32_t max_token(int codec) { return codec == FP_FSST8 ? 8u : 16u; }
+inline bool is_onpair(int codec) { return codec == FP_ONPAIR16 || codec == FP_ONPAIR12; }
+inline uint32_t max_token(int codec) { return is_onpair(codec) ? 16u : 8u; }
 inline uint32_t max_entries(int codec) {
-    return codec == FP_ONPAIR16 ? 65536u : codec == FP_ONPAIR12 ? 4096u : codec == FP_FSST8 ? 255u : 0u;
+    return codec == FP_ONPAIR16 ? 65536u : (codec == FP_ONPAIR12 || codec == FP_FSST12) ? 4096u
+                                         : codec == FP_FSST8 ? 255u : 0u;
 }
 inline uint32_t table_entries(int codec) {
-    return codec == FP_ONPAIR16 ? 65536u : codec == FP_ONPAIR12 ? 4096u : 256u;
+    return codec == FP_ONPAIR16 ? 65536u : (codec == FP_ONPAIR12 || codec == FP_FSST12) ? 4096u : 256u;
 }
-inline uint32_t table_stride(int codec) { return codec == FP_FSST8 ? 8u : 16u; }
+inline uint32_t table_stride(int codec) { return is_onpair(codec) ? 16u : 8u; }
+
+// The split-read rule of the paper (Sec. 4.3, gather width): read 8 bytes per token (W = 8)
+// unless more than 60 % of the tokens are longer than 8 bytes (W = 16).
+// hist[L] counts tokens of L bytes, L = 0..16.
+inline int width_for_histogram(const uint64_t* hist) {
+    uint64_t all = 0, long_ = 0;
+    for (int L = 0; L <= 16; ++L) {
+        all += hist[L];
+        if (L > 8) long_ += hist[L];
+    }
+    return (all > 0 && long_ * 5 > all * 3) ? 16 : 8;
+}
 
 }  // namespace fp
 
 // Opaque dictionary handle of the C ABI.
 struct fp_dict {
-    int codec;
-    int device;
-    uint32_t n_entries;
-    void* d_table;
-    uint8_t* d_lens;
-    uint8_t* d_bytes;
-    uint32_t* d_offsets;
-    size_t table_bytes;
+    int codec = 0;
+    int device = 0;
+    uint32_t n_entries = 0;
+    int width = 8;                 // dictionary read width fp_decode uses (8 or 16; FSST codecs: 8)
+    void* d_table = nullptr;
+    uint8_t* d_lens = nullptr;
+    void* d_planes = nullptr;      // OnPair: split planes (see DictView); else null
+    uint8_t* d_bytes = nullptr;
+    uint32_t* d_offsets = nullptr;
+    size_t table_bytes = 0;
     fp::DictView view() const {
-        return fp::DictView{d_table, d_lens, d_bytes, d_offsets, n_entries};
+        return fp::DictView{d_table, d_lens, d_planes, d_bytes, d_offsets, n_entries};
     }
 };

@@ -22,7 +22,7 @@ constexpr int kScanItems = 2048;   // strings per scan block (kBlock x 8)
 
 __device__ __forceinline__ u32 read_slot(int codec, const uint8_t* s, u64 q) {
     if (codec == FP_ONPAIR16) return (u32)s[2 * q] | ((u32)s[2 * q + 1] << 8);
-    if (codec == FP_ONPAIR12) {
+    if (codec == FP_ONPAIR12 || codec == FP_FSST12) {
         const u64 by = q * 3 / 2;
         const u32 a = s[by], b = s[by + 1];
         return (q & 1) ? ((a >> 4) | (b << 4)) : (a | ((b & 0xfu) << 8));

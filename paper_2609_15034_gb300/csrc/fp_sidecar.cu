@@ -39,6 +39,11 @@ struct Shape<FP_FSST8> {
     static constexpr int K = 32;
     static constexpr bool DSMEM = true;
 };
+template <>
+struct Shape<FP_FSST12> {
+    static constexpr int K = 16;
+    static constexpr bool DSMEM = true;   // 32 KiB of 8-byte entries
+};
 
 uint32_t tile_slots(int codec) { return codec == FP_FSST8 ? 32u * 32u : 32u * 16u; }
 
@@ -87,8 +92,11 @@ struct Path {
     static size_t decode_smem() {
         return (size_t)C::DICT_BYTES + (DSMEM ? (size_t)C::LENS_BYTES : 0) + kSidecarWarps * sizeof(WarpArea<K>);
     }
+    // dictionary reads: split planes for the staged OnPair-12 table, whole
+    // entries for OnPair-16 through L1, 8-byte entries for the FSST codecs
+    static constexpr int W = CODEC == FP_ONPAIR16 ? 16 : 8;
     static const void* decode_kernel() {
-        return (const void*)&warp_decode_kernel<CODEC, K, DSMEM, kSidecarWarps, 1>;
+        return (const void*)&warp_decode_kernel<CODEC, K, DSMEM, kSidecarWarps, 1, W>;
     }
     // Index pass in blocks [0, ib), reduce in the next rg blocks (rg = 0: index only).
     static cudaError_t index_reduce(const DecodeParams& p, Extent* xp, u64* agg, uint64_t ib, uint64_t rg,
@@ -129,9 +137,11 @@ fp_status device_setup(int codec, int* sms) {
     if (!done) {
         const void* k = codec == FP_ONPAIR16 ? Path<FP_ONPAIR16>::decode_kernel()
                         : codec == FP_ONPAIR12 ? Path<FP_ONPAIR12>::decode_kernel()
+                        : codec == FP_FSST12   ? Path<FP_FSST12>::decode_kernel()
                                                : Path<FP_FSST8>::decode_kernel();
         const size_t smem = codec == FP_ONPAIR16 ? Path<FP_ONPAIR16>::decode_smem()
                             : codec == FP_ONPAIR12 ? Path<FP_ONPAIR12>::decode_smem()
+                            : codec == FP_FSST12   ? Path<FP_FSST12>::decode_smem()
                                                    : Path<FP_FSST8>::decode_smem();
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sidecar decode)");
@@ -259,6 +269,7 @@ fp_status fp_sidecar_build(fp_codec codec, const fp_dict* dict, const void* d_co
     u64* ex = reinterpret_cast<u64*>(d_sidecar) + 1;
     if (codec == FP_ONPAIR16) e = build_launches<FP_ONPAIR16>(p, scratch, L, ex, sms, stream);
     else if (codec == FP_ONPAIR12) e = build_launches<FP_ONPAIR12>(p, scratch, L, ex, sms, stream);
+    else if (codec == FP_FSST12) e = build_launches<FP_FSST12>(p, scratch, L, ex, sms, stream);
     else e = build_launches<FP_FSST8>(p, scratch, L, ex, sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "sidecar build launch");
     return FP_OK;
@@ -290,6 +301,7 @@ fp_status fp_decode_sidecar(fp_codec codec, const fp_dict* dict, const void* d_c
     const u64* sc = reinterpret_cast<const u64*>(d_sidecar);
     if (codec == FP_ONPAIR16) e = decode_launches<FP_ONPAIR16>(p, scratch, L, sc, sms, stream);
     else if (codec == FP_ONPAIR12) e = decode_launches<FP_ONPAIR12>(p, scratch, L, sc, sms, stream);
+    else if (codec == FP_FSST12) e = decode_launches<FP_FSST12>(p, scratch, L, sc, sms, stream);
     else e = decode_launches<FP_FSST8>(p, scratch, L, sc, sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "sidecar decode launch");
     return FP_OK;

@@ -103,26 +103,35 @@ struct WarpArea {
     u32 lit_mask[32];       // FSST-8: bit k = slot k holds a literal byte
 };
 
-template <int CODEC, int K, bool DSMEM>
+// W: dictionary read width of the OnPair codecs (paper Sec. 3.2 and 4.3):
+// 16 reads whole 16-byte entries, 8 reads the low plane (bytes 0-7) for
+// every token and the high plane (bytes 8-15) only for longer tokens.  The
+// FSST codecs have 8-byte entries (W = 8).
+template <int CODEC, int K, bool DSMEM, int W = (CODEC == FP_ONPAIR16 || CODEC == FP_ONPAIR12) ? 16 : 8>
 struct WarpCore {
-    static constexpr bool FSST = (CODEC == FP_FSST8);
+    static constexpr bool FSST = (CODEC == FP_FSST8);   // escape codec: two-state scan elements
+    static constexpr bool TOK8 = (CODEC == FP_FSST8 || CODEC == FP_FSST12);   // 8-byte table entries
+    static constexpr bool W12 = (CODEC == FP_ONPAIR12 || CODEC == FP_FSST12);  // 12-bit codes
     static constexpr int TILE = 32 * K;
-    static constexpr int WBITS = (CODEC == FP_ONPAIR16) ? 16 : (CODEC == FP_ONPAIR12 ? 12 : 8);
+    static constexpr int WBITS = (CODEC == FP_ONPAIR16) ? 16 : (W12 ? 12 : 8);
     static constexpr int LANE_BYTES = K * WBITS / 8;   // code bytes of one lane
-    static constexpr int DICT_BYTES = DSMEM ? (FSST ? 256 * 8 : 4096 * 16) : 0;
-    static constexpr int LENS_BYTES = FSST ? 256 : (CODEC == FP_ONPAIR12 ? 4096 : 65536);
-    static constexpr int kTable = FSST ? 256 : 4096;   // entries of a table staged in shared memory
+    // entries of the table (a staged table, or the global planes)
+    static constexpr int kTable = (CODEC == FP_FSST8) ? 256 : (CODEC == FP_ONPAIR16 ? 65536 : 4096);
+    static constexpr int DICT_BYTES = DSMEM ? kTable * (TOK8 ? 8 : 16) : 0;
+    static constexpr int LENS_BYTES = kTable;
     typedef TileRegs<CODEC, K> R;
     static_assert(K == 8 || K == 16 || K == 32, "slots per lane");
     static_assert(!FSST || K >= 16, "FSST-8 handles 16 slots at a time");
     static_assert(!DSMEM || CODEC != FP_ONPAIR16, "OnPair-16 tables do not fit in shared memory");
     static_assert(LANE_BYTES % 8 == 0, "lane code bytes are read in 8-byte words");
+    static_assert(W == 16 || W == 8, "read width");
+    static_assert(!TOK8 || W == 8, "FSST entries are 8 bytes");
 
     static __device__ __forceinline__ u32 full_mask() { return K == 32 ? 0xffffffffu : ((1u << K) - 1u); }
 
     // ---- codes of slots [q0, q0 + K) ---------------------------------------
     static __device__ __forceinline__ void unpack_words(const u32* wv, R& r) {
-        if (CODEC == FP_ONPAIR12) {
+        if (W12) {
 #pragma unroll
             for (int g = 0; g < K / 8; ++g) {
                 const u32 a = wv[3 * g], bb = wv[3 * g + 1], c = wv[3 * g + 2];
@@ -172,7 +181,7 @@ struct WarpCore {
                 }
                 r.c[m] = v;
             }
-        } else if (CODEC == FP_ONPAIR12) {
+        } else if (W12) {
 #pragma unroll
             for (int m = 0; m < K / 2; ++m) {
                 u32 v = 0;
@@ -299,6 +308,24 @@ struct WarpCore {
         return TElem{c0, c1, s0 | (s1 << 1)};
     }
 
+    // Token of `code` (zero padded to 16 bytes).  OnPair: planes staged in
+    // shared memory (DSMEM) or read through L1 from the global planes (W = 8)
+    // or the 16-byte table (W = 16).  FSST-12: 8-byte entries.
+    static __device__ __forceinline__ uint4 token(const DecodeParams& p, const uint4* dict, u32 code, u32 len) {
+        if (TOK8) {
+            const uint2 d = DSMEM ? reinterpret_cast<const uint2*>(dict)[code]
+                                  : __ldg(reinterpret_cast<const uint2*>(p.dict.table) + code);
+            return make_uint4(d.x, d.y, 0u, 0u);
+        }
+        if (!DSMEM && W == 16) return __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
+        const uint2* lo = DSMEM ? reinterpret_cast<const uint2*>(dict) : reinterpret_cast<const uint2*>(p.dict.planes);
+        const uint2 a = DSMEM ? lo[code] : __ldg(lo + code);
+        uint2 b = make_uint2(0u, 0u);
+        // split read: the high plane only for longer tokens (W = 8), always for W = 16
+        if (W == 16 || len > 8u) b = DSMEM ? lo[kTable + code] : __ldg(lo + kTable + code);
+        return make_uint4(a.x, a.y, b.x, b.y);
+    }
+
     template <bool ALLV>
     static __device__ __forceinline__ void assemble_onpair(const DecodeParams& p, const uint4* dict, const R& r,
                                                            Assembler& as) {
@@ -306,19 +333,8 @@ struct WarpCore {
         for (int k0 = 0; k0 < K; k0 += 4) {
             uint4 tok[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const u32 code = code_at<CODEC, K>(r, k0 + h);
-                if (DSMEM) {
-                    // split read: the low 8 bytes always, the high 8 only for longer tokens
-                    const uint2* lo = reinterpret_cast<const uint2*>(dict);
-                    const uint2 a = lo[code];
-                    uint2 b = make_uint2(0u, 0u);
-                    if (len_at<CODEC, K>(r, k0 + h) > 8u) b = lo[kTable + code];
-                    tok[h] = make_uint4(a.x, a.y, b.x, b.y);
-                } else {
-                    tok[h] = __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
-                }
-            }
+            for (int h = 0; h < 4; ++h)
+                tok[h] = token(p, dict, code_at<CODEC, K>(r, k0 + h), len_at<CODEC, K>(r, k0 + h));
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const int k = k0 + h;
@@ -398,14 +414,21 @@ struct WarpCore {
 
     // Decode warp tile t of column (p, x) from its fetched inputs: offset
     // and entering escape state (from the tile scan), code words, string
-    // boundaries.  `area` is the warp's scratch.
+    // boundaries.  `area` is the warp's scratch.  `ex_tiles` holds the
+    // column's scanned tile offsets (f.ex = ex_tiles[t]): the tile's own
+    // byte total, recomputed here, must bring it to ex_tiles[t + 1], else
+    // ERRB_MISMATCH is raised (a self-check of the two passes, one load
+    // per tile).
     static __device__ __forceinline__ void decode_tile(const DecodeParams& p, const Extent& x, u64 t, const Fetch& f,
-                                                       const uint4* dict, const uint8_t* lens, WarpArea<K>& area,
-                                                       u32& err) {
+                                                       const u64* ex_tiles, const uint4* dict, const uint8_t* lens,
+                                                       WarpArea<K>& area, u32& err) {
         const u32 lane = threadIdx.x & 31u;
         const u64 tile_start = (x.first_tile + t) * (u64)TILE;
         const u64 q0 = tile_start + (u64)lane * K;
         const u64 ex = f.ex;
+        // low word of the next tile's offset (lane 0 checks), in flight during the tile
+        const bool chk = lane == 0u && t + 1 < x.n_tiles;
+        const u32 ex_next = chk ? __ldg(reinterpret_cast<const u32*>(ex_tiles + t + 1)) : 0u;
         R r;
         finish_load(p, x, q0, f.wv, f.fast, lens, r);
         r.t = (u32)t;
@@ -544,6 +567,7 @@ struct WarpCore {
             if (st) err |= ERRB_CORRUPT;   // a string would start on a literal
             if (!p.size_only) __stcs(p.out_offsets + i, (u32)(tile_excl + rel));
         }
+        if (chk && ex_next != (u32)tile_incl) err |= ERRB_MISMATCH;
         __syncwarp();   // the area is reused by the next tile
     }
 };
@@ -731,27 +755,19 @@ __global__ void __launch_bounds__(256) tiles_scan_kernel(const DecodeParams p, c
 // ---------------------------------------------------------------------------
 // Pass 3: every warp decodes warp tiles on its own (grid-stride order).
 // ---------------------------------------------------------------------------
-template <int CODEC, int K, bool DSMEM, int NW, int MINB>
+template <int CODEC, int K, bool DSMEM, int NW, int MINB, int W = WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16>
 __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const DecodeParams p, const Extent* xp,
                                                                      const u64* ex) {
-    typedef WarpCore<CODEC, K, DSMEM> C;
+    typedef WarpCore<CODEC, K, DSMEM, W> C;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint4* s_dict = reinterpret_cast<uint4*>(smem_raw);
     uint8_t* s_lens = smem_raw + C::DICT_BYTES;
     WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
     if (DSMEM) {
-        const uint4* src = reinterpret_cast<const uint4*>(p.dict.table);
-        if (C::FSST) {
-            for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
-        } else {
-            // OnPair: entry e's bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e
-            uint2* planes = reinterpret_cast<uint2*>(s_dict);
-            for (int i = threadIdx.x; i < C::kTable; i += NW * 32) {
-                const uint4 v = __ldg(src + i);
-                planes[i] = make_uint2(v.x, v.y);
-                planes[C::kTable + i] = make_uint2(v.z, v.w);
-            }
-        }
+        // FSST: the 8-byte entries as they are; OnPair: the two planes (entry
+        // e's bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e)
+        const uint4* src = reinterpret_cast<const uint4*>(C::TOK8 ? p.dict.table : p.dict.planes);
+        for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
         const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
         for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
         __syncthreads();
@@ -776,7 +792,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
             u32 lo2 = 0, hi2 = 0;
             if (tn < x.n_tiles) C::fetch(p, x, ex, tn, lo1, hi1, nxt);
             if (t2 < x.n_tiles) C::bounds(p, t2, lo2, hi2);
-            C::decode_tile(p, x, t, cur, s_dict, lens, area, err);
+            C::decode_tile(p, x, t, cur, ex, s_dict, lens, area, err);
             cur = nxt;
             lo1 = lo2;
             hi1 = hi2;

@@ -14,18 +14,20 @@ column is reproducible from its key.
 Codec formats follow the paper's Sec. 2.1: OnPair-16 and OnPair-12 use 16-
 and 12-bit codes into dictionaries of up to 65,536 / 4,096 tokens of at most
 16 bytes; FSST-8 uses byte codes into a 255-symbol table of tokens of at most
-8 bytes, with code 255 reserved as an escape followed by one literal byte.
+8 bytes, with code 255 reserved as an escape followed by one literal byte;
+FSST-12 uses 12-bit codes (stored like OnPair-12) into a table of up to 4,096
+symbols of at most 8 bytes, with no escape.
 """
 from __future__ import annotations
 
 import dataclasses
 import numpy as np
 
-ONPAIR16, ONPAIR12, FSST8 = 1, 2, 3
-CODEC_NAMES = {ONPAIR16: "onpair16", ONPAIR12: "onpair12", FSST8: "fsst8"}
-CODE_BITS = {ONPAIR16: 16, ONPAIR12: 12, FSST8: 8}
-MAX_TOKEN = {ONPAIR16: 16, ONPAIR12: 16, FSST8: 8}
-MAX_ENTRIES = {ONPAIR16: 65536, ONPAIR12: 4096, FSST8: 255}
+ONPAIR16, ONPAIR12, FSST8, FSST12 = 1, 2, 3, 4
+CODEC_NAMES = {ONPAIR16: "onpair16", ONPAIR12: "onpair12", FSST8: "fsst8", FSST12: "fsst12"}
+CODE_BITS = {ONPAIR16: 16, ONPAIR12: 12, FSST8: 8, FSST12: 12}
+MAX_TOKEN = {ONPAIR16: 16, ONPAIR12: 16, FSST8: 8, FSST12: 8}
+MAX_ENTRIES = {ONPAIR16: 65536, ONPAIR12: 4096, FSST8: 255, FSST12: 4096}
 FSST_ESCAPE = 255
 
 ALPHABET64 = np.frombuffer(
@@ -274,6 +276,18 @@ def fsst8_dictionary(seed: int) -> Dictionary:
     return Dictionary.from_tokens(FSST8, _url_tokens(rng, 255))
 
 
+def fsst12_dictionary(seed: int) -> Dictionary:
+    """4,096 symbols: codes 0..255 are the one-byte symbols (an escape-free
+    table must cover every byte), codes 256..4095 distinct URL/identifier-
+    like symbols of 2..8 bytes."""
+    rng = rng_for(4, seed, 0)
+    multi = [t for t in _url_tokens(rng, 6000) if len(t) >= 2][:4096 - 256]
+    while len(multi) < 4096 - 256:
+        extra = [t for t in _url_tokens(rng, 2000) if len(t) >= 2 and t not in set(multi)]
+        multi += extra[:4096 - 256 - len(multi)]
+    return Dictionary.from_tokens(FSST12, [bytes([b]) for b in range(256)] + multi)
+
+
 # ---------------------------------------------------------------------------
 # Columns
 # ---------------------------------------------------------------------------
@@ -391,12 +405,35 @@ def fsst8_column(seed: int = 0, n_strings: int = 16_000_000, dictionary=None,
                   name=f"fsst8 seed={seed} n={n_strings}")
 
 
+def fsst12_column(seed: int = 0, n_strings: int = 16_000_000, dictionary=None,
+                  median: float = 40.0, sigma: float = 0.6, zipf_s: float = 1.0) -> Column:
+    """Lognormal target lengths (median, sigma), at least 1 byte; every code
+    is a symbol drawn Zipf(zipf_s) over the whole table through a seeded
+    permutation (no escapes).  The last symbol may overshoot the target."""
+    d = dictionary if dictionary is not None else fsst12_dictionary(seed)
+    rng = rng_for(4, seed, 1)
+    perm = rng.permutation(d.n_entries).astype(np.uint16)
+    cdf = zipf_cdf(d.n_entries, zipf_s)
+    tok_len = d.token_lengths().astype(np.int64)
+
+    def draw(rng, remaining):
+        c = perm[zipf_draw(rng, cdf, remaining.size)]
+        return c, tok_len[c], None
+
+    targets = np.maximum(1, np.rint(median * np.exp(sigma * rng.standard_normal(n_strings)))).astype(np.int64)
+    codes, _, starts = _fill_rounds(rng, targets, draw)
+    return Column(FSST12, d, pack12(codes), starts.astype(np.uint32), int(codes.size),
+                  slot_codes=codes, slot_is_literal=np.zeros(codes.size, bool),
+                  name=f"fsst12 seed={seed} n={n_strings}")
+
+
 # Full-size workloads (seed 0) and the small parity cases built with the same
 # recipe.
 WORKLOADS = {
     "onpair16_100k": lambda seed=0: onpair16_column(seed, 100_000),
     "onpair12_10m": lambda seed=0: onpair12_column(seed, 10_000_000),
     "fsst8_16m": lambda seed=0: fsst8_column(seed, 16_000_000),
+    "fsst12_16m": lambda seed=0: fsst12_column(seed, 16_000_000),
 }
 
 
@@ -407,6 +444,8 @@ def column(codec: int, seed: int, n_strings: int, **kw) -> Column:
         return onpair12_column(seed, n_strings, **kw)
     if codec == FSST8:
         return fsst8_column(seed, n_strings, **kw)
+    if codec == FSST12:
+        return fsst12_column(seed, n_strings, **kw)
     raise ValueError(codec)
 
 

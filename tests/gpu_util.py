@@ -15,7 +15,7 @@ def store_slots(codec: int, slots) -> np.ndarray:
     slots = np.asarray(slots, np.uint16)
     if codec == synth.ONPAIR16:
         return synth.pack16(slots)
-    if codec == synth.ONPAIR12:
+    if codec in (synth.ONPAIR12, synth.FSST12):
         return synth.pack12(slots)
     return slots.astype(np.uint8)
 

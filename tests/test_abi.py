@@ -98,3 +98,35 @@ def test_batch_configuration_table():
         assert info["blocks_per_sm"] >= 1
     with pytest.raises(fp.FastPairError):
         fp.batch_config_info(n)
+
+
+def test_split_read_rule_against_the_papers_columns():
+    """fp_width_for_histogram applies the rule of the paper's Sec. 4.3 (read
+    8 bytes per token unless more than 60 % of the tokens exceed 8 bytes).
+    Pinned at its boundary and on the share of tokens of at most 8 bytes that
+    Table 1 prints for real columns: the rule keeps split reads for columns
+    like ClickBench URL (51 % short) and Loghub HDFS (48 %) and turns them off
+    for Loghub Spark (21 %), TPC-H l_comment (33 %) and o_clerk (0 %)."""
+    import paper_2609_15034_gb300 as fp
+
+    def hist(short_pct):
+        h = [0] * 17
+        h[5] = short_pct
+        h[12] = 100 - short_pct
+        return h
+
+    assert fp.width_for_histogram([0] * 17) == 8
+    assert fp.width_for_histogram(hist(40)) == 8     # exactly 60 % long: not more than 60 %
+    assert fp.width_for_histogram(hist(39)) == 16
+    h = [0] * 17
+    h[8], h[9] = 2, 3                                # 60 % long, the boundary between 8 and 9 bytes
+    assert fp.width_for_histogram(h) == 8
+    h[9] = 4
+    assert fp.width_for_histogram(h) == 16
+    table1_short = {"ClickBench URL (OnPair-16)": 51, "Loghub HDFS (OnPair-16)": 48,
+                    "Loghub Android (OnPair-16)": 43, "c_address (OnPair-16)": 100,
+                    "Loghub Spark (OnPair-16)": 21, "l_comment (OnPair-16)": 33, "o_clerk (OnPair-16)": 0,
+                    "Loghub Windows (OnPair-12)": 37, "Loghub Spark (OnPair-12)": 42}
+    expect16 = {k for k, v in table1_short.items() if v < 40}
+    for name, pct in table1_short.items():
+        assert (fp.width_for_histogram(hist(pct)) == 16) == (name in expect16), name

@@ -257,3 +257,39 @@ def test_batch_large_chunks(fp):
         for it in items:
             it.check()
         plan.destroy()
+
+
+def test_batch_with_fsst12_chunks(fp):
+    """FSST-12 chunks (the paper's escape-free 12-bit codec) in a mixed batch:
+    decoded by every warp-tile configuration like the other codecs; the
+    block-pipeline configurations, which have no FSST-12 queue, reject the
+    plan, and the tuner skips them."""
+    FSST12 = synth.FSST12
+    items = mixed_items(fp, 3)
+    for k, n in enumerate((1, 2, 700, 20000, 90000)):
+        items.append(BatchItem(fp, synth.column(FSST12, 950 + k, n)))
+    col = synth.column(FSST12, 960, 12000)
+    items.append(BatchItem(fp, col, code_offsets=col.code_offsets[777:9001 + 1]))
+    items.append(BatchItem(fp, col, code_offsets=col.code_offsets[5:6]))   # no strings
+    chunks = [it.chunk(fp) for it in items]
+    for cfg in range(fp.batch_config_count()):
+        if not fp.batch_config_info(cfg)["warp_tiles"]:
+            with pytest.raises(fp.FastPairError):
+                fp.Plan(chunks, config=cfg)
+            continue
+        plan, st, sts, tot = run_plan(fp, items, config=cfg)
+        assert st == fp.OK, (cfg, fp.last_error())
+        assert plan.info()["slots_per_thread_fsst12"] > 0
+        for it, t in zip(items, tot):
+            assert int(t) == it.ref.total
+            it.check(f"config {cfg}")
+        plan.destroy()
+    plan, st, _, _ = run_plan(fp, items)
+    assert st == fp.OK
+    info = plan.info()
+    assert fp.batch_config_info(info["config"])["warp_tiles"]
+    for c, ms in enumerate(info["tune_ms"]):
+        assert (ms > 0) == fp.batch_config_info(c)["warp_tiles"], (c, ms)
+    for it in items:
+        it.check("tuned")
+    plan.destroy()

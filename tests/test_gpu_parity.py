@@ -1,7 +1,9 @@
 """GPU parity: the CUDA path, called through the C ABI, against the CPU
 oracle, byte for byte and offset for offset (decoding is exact; there is no
 tolerance).  Sizes span several tiles with ragged tails; adversarial cases
-cover empty inputs, tile-edge alignments, FSST-8 escape runs and errors."""
+cover empty inputs, tile-edge alignments, FSST-8 escape runs and errors.
+Every codec: OnPair-16, OnPair-12, FSST-8 and FSST-12 (the paper's
+escape-free 12-bit codec, Sec. 2.1)."""
 import numpy as np
 import pytest
 
@@ -11,8 +13,8 @@ from gpu_util import DeviceColumn, assert_same, make_column, oracle_decode
 
 pytestmark = pytest.mark.gpu
 
-ONPAIR16, ONPAIR12, FSST8 = synth.ONPAIR16, synth.ONPAIR12, synth.FSST8
-CODECS = [ONPAIR16, ONPAIR12, FSST8]
+ONPAIR16, ONPAIR12, FSST8, FSST12 = synth.ONPAIR16, synth.ONPAIR12, synth.FSST8, synth.FSST12
+CODECS = [ONPAIR16, ONPAIR12, FSST8, FSST12]
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +46,7 @@ def each_variant(fp, codec):
 @pytest.mark.parametrize("codec", CODECS)
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_generated_columns_all_variants(fp, codec, seed):
-    n = {ONPAIR16: 7001, ONPAIR12: 3001, FSST8: 9001}[codec]
+    n = {ONPAIR16: 7001, ONPAIR12: 3001, FSST8: 9001, FSST12: 8001}[codec]
     col = synth.column(codec, seed, n)
     dc = DeviceColumn(col)
     for v in variants(fp, codec):
@@ -239,7 +241,7 @@ def test_fsst8_escape_runs_across_tiles(fp):
 # errors: reported through fp_sync_status, writes stay in bounds
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("codec", [ONPAIR16, ONPAIR12])
+@pytest.mark.parametrize("codec", [ONPAIR16, ONPAIR12, FSST12])
 def test_corrupt_code(fp, codec):
     col = make_column(codec, [b"a", b"bc"], [0, 1, 5, 1] * 3000, [0, 6000, 12000])
     dc = DeviceColumn(col)
@@ -320,3 +322,48 @@ def test_two_streams_concurrently(fp):
         assert fp.sync_status(s.cuda_stream) == fp.OK
         np.testing.assert_array_equal(out.cpu().numpy(), ref.data)
         np.testing.assert_array_equal(offs.cpu().numpy().view(np.uint32), ref.offsets)
+
+
+# --------------------------------------------------------------------------
+# dictionary read width W (paper Sec. 3.2 split planes, Sec. 4.3 rule)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("codec", [ONPAIR16, ONPAIR12])
+def test_read_width_from_the_dictionary_and_both_widths_decode_alike(fp, codec):
+    rng = np.random.default_rng(40 + codec)
+    short = _tokens(codec, rng, 300, 1, 8)
+    long_ = _tokens(codec, rng, 300, 9, 16)
+    # the upload applies the rule to the dictionary's entries: W = 16 only
+    # when more than 60 % of them exceed 8 bytes
+    for toks, w in ((short, 8), (long_, 16), (short[:150] + long_[:150], 8),
+                    (short[:119] + long_[:181], 16), (short[:120] + long_[:180], 8)):
+        d = fp.Dict(codec, np.frombuffer(b"".join(toks), np.uint8),
+                    np.concatenate([[0], np.cumsum([len(t) for t in toks])]).astype(np.uint32))
+        assert d.width == w, (len(toks), w)
+        d.free()
+    toks = short[:100] + long_[:200]
+    slots = rng.integers(0, len(toks), 60000)
+    cuts = np.sort(rng.integers(0, slots.size, 4000))
+    col = make_column(codec, toks, slots, np.concatenate([[0], cuts, [slots.size]]))
+    dc = DeviceColumn(col)
+    assert dc.dict.width == 16
+    for w in (16, 8, 16):
+        dc.dict.set_width(w)
+        assert dc.dict.width == w
+        v = fp.variant_for_dict(dc.dict, dc.codes_bytes)
+        assert fp.variant_width(codec, v) == w
+        assert_same(col, dc)
+    with pytest.raises(fp.FastPairError):
+        dc.dict.set_width(12)
+
+
+def test_fsst_dictionaries_read_8_bytes(fp):
+    for codec in (FSST8, FSST12):
+        col = synth.column(codec, 3, 10)
+        d = fp.Dict(codec, col.dictionary.data, col.dictionary.offsets)
+        assert d.width == 8
+        with pytest.raises(fp.FastPairError):
+            d.set_width(16)
+        for v in range(fp.variant_count(codec)):
+            assert fp.variant_width(codec, v) == 8
+        d.free()

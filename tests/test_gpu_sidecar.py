@@ -12,7 +12,8 @@ from gpu_util import GUARD, GUARD_BYTES, DeviceColumn
 
 pytestmark = pytest.mark.gpu
 
-ONPAIR16, ONPAIR12, FSST8 = synth.ONPAIR16, synth.ONPAIR12, synth.FSST8
+ONPAIR16, ONPAIR12, FSST8, FSST12 = synth.ONPAIR16, synth.ONPAIR12, synth.FSST8, synth.FSST12
+CODECS = [ONPAIR16, ONPAIR12, FSST8, FSST12]
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +27,7 @@ def fp():
 
 def cases():
     out = []
-    for codec in (ONPAIR16, ONPAIR12, FSST8):
+    for codec in CODECS:
         for k, n in enumerate((1, 5, 300, 5000, 40000)):
             out.append((codec, 1000 + 10 * codec + k, n, None))
         out.append((codec, 1100 + codec, 20000, (1234, 17001)))   # a slice: code_offsets start mid-buffer
@@ -95,7 +96,7 @@ def test_decode_from_built_and_from_oracle_tables(fp, spec):
         np.testing.assert_array_equal(data, c.ref.data)
 
 
-@pytest.mark.parametrize("codec", [ONPAIR16, ONPAIR12, FSST8])
+@pytest.mark.parametrize("codec", CODECS)
 def test_capacity_is_reported_and_respected(fp, codec):
     c = Case(fp, (codec, 1300 + codec, 3000, None))
     c.sc.build()
@@ -104,8 +105,11 @@ def test_capacity_is_reported_and_respected(fp, codec):
     assert guard_ok
 
 
-@pytest.mark.parametrize("codec", [ONPAIR16, ONPAIR12, FSST8])
+@pytest.mark.parametrize("codec", CODECS)
 def test_foreign_table_stays_in_bounds(fp, codec):
+    """A table from elsewhere: every write stays in bounds, and the decode's
+    self-check (each tile's recomputed byte total against the next entry)
+    reports the mismatch (bit 16)."""
     import torch
     c = Case(fp, (codec, 1400 + codec, 3000, None))
     rng = np.random.default_rng(codec)
@@ -115,6 +119,7 @@ def test_foreign_table_stays_in_bounds(fp, codec):
         t[0] = c.ref.total   # size entry consistent, positions not
         bits, data, offs, guard_ok = c.decode(fp, table=torch.from_numpy(t.view(np.int64)).cuda())
         assert guard_ok
+        assert bits & 16, bits
 
 
 def test_arguments_are_checked(fp):
