@@ -100,10 +100,10 @@ typedef struct fp_dict fp_dict;
  * OnPair dictionaries are also stored as two planes (bytes 0-7 and 8-15 of
  * every entry, paper Sec. 3.2) and carry a read width W: 8 = split read
  * (the low plane for every token, the high plane only for tokens longer
- * than 8 bytes), 16 = whole entries.  The upload sets W by the paper's rule
- * (Sec. 4.3: W = 8 unless more than 60 % of the tokens exceed 8 bytes)
- * applied to the dictionary's own entries; fp_dict_set_width overrides it,
- * e.g. with fp_width_for_histogram of a column's token-length histogram.
+ * than 8 bytes), 16 = whole entries.  The upload sets W = 16, the faster
+ * width on GB300 for every share of long tokens measured; the paper's rule
+ * (Sec. 4.3: W = 8 unless more than 60 % of the tokens exceed 8 bytes) is
+ * fp_width_for_histogram, and fp_dict_set_width applies either choice.
  *
  * Errors: FP_ERR_ARG if a token length is outside 1..16 (OnPair) or 1..8
  * (FSST-8, FSST-12), n_entries is out of range or a pointer is NULL;

@@ -369,10 +369,14 @@ fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t*
     d->codec = codec;
     d->n_entries = n_entries;
     d->table_bytes = table.size();
-    // OnPair: the two 8-byte planes of the entries, and the read width by the
-    // paper's rule over the dictionary's own token lengths
+    // OnPair: the two 8-byte planes of the entries (for split reads) and the
+    // read width.  The default is 16: on GB300 this decoder read whole
+    // entries faster than split reads for every share of long tokens from 0
+    // to 100 % (1-3 % with the table in shared memory, 5-13 % through L1), so
+    // the paper's rule (fp_width_for_histogram) is left to callers, through
+    // fp_dict_set_width.
     std::vector<uint8_t> planes;
-    d->width = 8;
+    d->width = is_onpair(codec) ? 16 : 8;
     if (is_onpair(codec)) {
         const size_t n_tab = table_entries(codec);
         planes.resize(n_tab * 16);
@@ -380,9 +384,6 @@ fp_status fp_dict_upload(fp_codec codec, const uint8_t* h_bytes, const uint32_t*
             memcpy(&planes[i * 8], &table[i * 16], 8);
             memcpy(&planes[(n_tab + i) * 8], &table[i * 16 + 8], 8);
         }
-        uint64_t hist[17] = {0};
-        for (uint32_t i = 0; i < n_entries; ++i) hist[lens[i]] += 1;
-        d->width = width_for_histogram(hist);
     }
     cudaError_t e = cudaGetDevice(&d->device);
     if (e == cudaSuccess) e = cudaMalloc(&d->d_table, table.size());

@@ -116,17 +116,9 @@ __device__ __forceinline__ void reduce_queue(const BatchParams& bp, int q, u64 t
         typename C::R r;
         C::finish_load(p, x, q0, wv, fast, p.dict.lens, r);
         u32 err = 0;
-        const TElem e = C::element(r, err);
-        // every codec's element in the two-state form (OnPair: both states
-        // alike, the tile's byte count as a plain warp sum)
-        TElem inc;
-        if (C::FSST) {
-            inc = warp_scan_incl<true>(e, lane, telem_identity());
-        } else {
-            const u32 sum = __reduce_add_sync(0xffffffffu, e.b0);
-            inc = TElem{sum, sum, 2u};
-        }
-        if (lane == 31) bp.agg[rc->wt_base + (t - rc->tile_base)] = wt_pack<true>(inc);
+        // every codec's element in the two-state form (OnPair: both states alike)
+        const TElem e = C::tile_element(r, lane, err);
+        if (lane == 31) bp.agg[rc->wt_base + (t - rc->tile_base)] = wt_pack<true>(e);
         if (err) atomicOr(p.err_word, err);
         rc = rn;
         rn = r2;

@@ -57,7 +57,9 @@ const Variant* variant_get(int codec, int v) {
 // through L1 (20 warps; staging it per block does not pay: 637 vs 613 GB/s
 // at 300k strings); FSST-8 below 2^22 slots uses 16-slot lanes.  The OnPair
 // codecs come in both read widths (split read W = 8, whole entries W = 16);
-// the dictionary's width picks between them.
+// the dictionary's width picks between them.  FSST-12 stages its 32 KiB
+// table in shared memory at every size (16M strings: 1,134 GB/s with 32-slot
+// lanes, 1,113 with 16; 300k strings: 368 against 337 through L1).
 int variant_default(int codec, uint64_t max_slots, int width) {
     const bool split = width != 16;
     switch (codec) {
@@ -66,7 +68,7 @@ int variant_default(int codec, uint64_t max_slots, int width) {
             return split ? 9 : 7;
         case FP_ONPAIR16: return split ? 5 : 4;
         case FP_FSST8: return max_slots >= (1ull << 22) ? 4 : 2;
-        case FP_FSST12: return max_slots >= (1ull << 23) ? 0 : 1;
+        case FP_FSST12: return max_slots >= (1ull << 23) ? 2 : 0;
         default: return 0;
     }
 }
@@ -84,6 +86,23 @@ uint64_t variant_tile(const Variant& v) {
 }
 
 namespace {
+
+// Launch with programmatic stream serialization: the kernel may begin while
+// the previous kernel on the stream finishes; it calls grid_wait() before it
+// reads that kernel's results.
+cudaError_t launch_after(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, func, args);
+}
 
 constexpr size_t kExtentBytes = 64;
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -141,7 +160,10 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
         return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
     }
 
-    // warp tiles: index pass + reduce in one launch, tile scan, decode
+    // warp tiles: index pass + reduce in one launch, tile scan, decode.  The
+    // first launch waits for everything before it (the previous call's decode
+    // still reads this workspace); the next two may start early and wait in
+    // the kernel for their predecessor.
     Extent* xp = reinterpret_cast<Extent*>(base + L.o_extent);
     u64* agg = reinterpret_cast<u64*>(base + L.o_agg);
     u64* ex = reinterpret_cast<u64*>(base + L.o_ex);
@@ -159,14 +181,14 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
     const u64* cagg = agg;
     unsigned long long* st = p.tile_status;
     void* sargs[] = {(void*)&p, (void*)&cxp, (void*)&cagg, (void*)&ex, (void*)&st};
-    e = cudaLaunchKernel(var.scan, dim3((unsigned)sg), dim3(256), sargs, 0, stream);
+    e = launch_after(var.scan, dim3((unsigned)sg), dim3(256), sargs, 0, stream);
     if (e != cudaSuccess) return e;
     const u64* cex = ex;
     void* dargs[] = {(void*)&p, (void*)&cxp, (void*)&cex};
     const int nw = var.threads / 32;
     uint64_t dg = (n_wt_max + nw - 1) / nw;
     if (dg > (uint64_t)grid) dg = (uint64_t)grid;
-    return cudaLaunchKernel(var.kernel, dim3((unsigned)dg), dim3(var.threads), dargs, var.smem_bytes, stream);
+    return launch_after(var.kernel, dim3((unsigned)dg), dim3(var.threads), dargs, var.smem_bytes, stream);
 }
 
 }  // namespace fp

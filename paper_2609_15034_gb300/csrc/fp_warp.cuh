@@ -98,7 +98,7 @@ struct WarpArea {
     uint4 fa[32];
     uint4 fb[32];
     u32 meta[32];
-    u32 thr_excl[32];       // tile-relative output offset of each lane
+    u32 pre[K / 4][32];     // tile-relative output offset of slot 4m of each lane
     u32 contrib[K / 4][32]; // bytes each slot produced, one byte per slot
     u32 lit_mask[32];       // FSST-8: bit k = slot k holds a literal byte
 };
@@ -256,8 +256,65 @@ struct WarpCore {
         return n;
     }
 
-    // The lane's scan element; corrupt codes set ERRB_CORRUPT in err.
-    static __device__ __forceinline__ TElem element(const R& r, u32& err) {
+    // FSST-8 escape state across lanes.  A lane maps the state entering it
+    // (1: its first slot is a literal) to the state after it.  For a lane
+    // whose K slots are all 0xFF that map is the identity (codes and
+    // literals alternate, K is even); for any other lane it is constant: a
+    // slot that is not 0xFF (or lies outside the column, which resets the
+    // state) fixes the parity of every later slot.  x0 is the state after
+    // the lane entered with 0; `ident` marks the identity lanes.
+    static __device__ __forceinline__ void lane_state(const R& r, bool allv, u32 E, u32& x0, bool& ident) {
+        if (allv) {
+            u32 lit, esc;
+            fsst_escapes<K>(E, 0u, lit, esc);
+            x0 = (esc >> (K - 1)) & 1u;
+            ident = (E == full_mask());
+            return;
+        }
+        u32 st = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool v = (r.valid >> k) & 1u;
+            st = v ? (st ? 0u : (code_at<CODEC, K>(r, k) == 255u ? 1u : 0u)) : 0u;
+        }
+        x0 = st;
+        ident = false;
+    }
+    // The state entering this lane when s_tile enters the tile: the exit of
+    // the nearest lower lane whose map is constant, else s_tile (only
+    // identity lanes before it).  One ballot and one shuffle; every lane of
+    // the warp calls it.
+    static __device__ __forceinline__ u32 enter_state(u32 cmask, u32 x0, u32 s_tile, u32 lane) {
+        const u32 below = cmask & ((1u << lane) - 1u);
+        const u32 src = below ? 31u - (u32)__clz(below) : 0u;
+        const u32 xk = __shfl_sync(0xffffffffu, x0, src);
+        return below ? xk : s_tile;
+    }
+    // Bytes of an all-inside lane entered in state s (lit/esc: its literal
+    // and escape-code slots).
+    static __device__ __forceinline__ u32 fsst_lane_bytes(const R& r, u32 E, u32 s) {
+        u32 lit, esc;
+        fsst_escapes<K>(E, s, lit, esc);
+        return fsst_bytes(r, ~(lit | esc) & full_mask(), lit);
+    }
+    // Bytes of an edge lane (some slots outside the column) entered in state s.
+    static __device__ __forceinline__ u32 fsst_edge_bytes(const R& r, u32 s) {
+        u32 n = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool v = (r.valid >> k) & 1u;
+            const bool is255 = code_at<CODEC, K>(r, k) == 255u;
+            n += v ? (s ? 1u : (is255 ? 0u : len_at<CODEC, K>(r, k))) : 0u;
+            s = v ? (s ? 0u : (is255 ? 1u : 0u)) : 0u;
+        }
+        return n;
+    }
+
+    // The warp tile's scan element; every lane of the warp calls it.  OnPair:
+    // the tile's byte count (the same for both entry states; corrupt codes
+    // set ERRB_CORRUPT).  FSST-8: for each escape state entering the tile,
+    // the bytes it produces and the state after it.
+    static __device__ __forceinline__ TElem tile_element(const R& r, u32 lane, u32& err) {
         const bool allv = (r.valid == full_mask());
         if (!FSST) {
             u32 sum = 0;
@@ -277,35 +334,25 @@ struct WarpCore {
                     if (__vcmpeq4(r.L[j], 0u) & vm) err |= ERRB_CORRUPT;
                 }
             }
-            return TElem{sum, 0u, 0u};
+            sum = __reduce_add_sync(0xffffffffu, sum);
+            return TElem{sum, sum, 2u};
         }
-        if (allv) {
-            const u32 E = ff_mask(r);
-            u32 lit0, esc0, lit1, esc1;
-            fsst_escapes<K>(E, 0u, lit0, esc0);
-            fsst_escapes<K>(E, 1u, lit1, esc1);
-            const u32 c0 = fsst_bytes(r, ~(lit0 | esc0) & full_mask(), lit0);
-            const u32 c1 = fsst_bytes(r, ~(lit1 | esc1) & full_mask(), lit1);
-            return TElem{c0, c1, ((esc0 >> (K - 1)) & 1u) | (((esc1 >> (K - 1)) & 1u) << 1)};
-        }
-        // slots outside the column reset the state (the column starts on a code)
-        u32 c0 = 0, c1 = 0, s0 = 0, s1 = 1;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const bool v = (r.valid >> k) & 1u;
-            const u32 bt = code_at<CODEC, K>(r, k);
-            const u32 L = len_at<CODEC, K>(r, k);
-            const bool is255 = (bt == 255u);
-            const u32 a0 = s0 ? 1u : (is255 ? 0u : L);
-            const u32 n0 = s0 ? 0u : (is255 ? 1u : 0u);
-            const u32 a1 = s1 ? 1u : (is255 ? 0u : L);
-            const u32 n1 = s1 ? 0u : (is255 ? 1u : 0u);
-            c0 += v ? a0 : 0u;
-            c1 += v ? a1 : 0u;
-            s0 = v ? n0 : 0u;
-            s1 = v ? n1 : 0u;
-        }
-        return TElem{c0, c1, s0 | (s1 << 1)};
+        const u32 E = allv ? ff_mask(r) : 0u;
+        u32 x0;
+        bool ident;
+        lane_state(r, allv, E, x0, ident);
+        // states entering this lane when the tile is entered with 0 and with 1:
+        // they differ only for lanes that only identity lanes precede
+        const u32 below = __ballot_sync(0xffffffffu, !ident) & ((1u << lane) - 1u);
+        const u32 xk = __shfl_sync(0xffffffffu, x0, below ? 31u - (u32)__clz(below) : 0u);
+        const u32 s0 = below ? xk : 0u, s1 = below ? xk : 1u;
+        u32 b0 = allv ? fsst_lane_bytes(r, E, s0) : fsst_edge_bytes(r, s0);
+        u32 b1 = b0;
+        if (__any_sync(0xffffffffu, s0 != s1) && s0 != s1) b1 = allv ? fsst_lane_bytes(r, E, s1) : fsst_edge_bytes(r, s1);
+        b0 = __reduce_add_sync(0xffffffffu, b0);
+        b1 = __reduce_add_sync(0xffffffffu, b1);
+        const u32 e = (ident ? s0 : x0) | ((ident ? s1 : x0) << 1);
+        return TElem{b0, b1, __shfl_sync(0xffffffffu, e, 31)};
     }
 
     // Token of `code` (zero padded to 16 bytes).  OnPair: planes staged in
@@ -434,42 +481,38 @@ struct WarpCore {
         r.t = (u32)t;
         r.tile_start = tile_start;
         const bool allv = (r.valid == full_mask());
-        const TElem e = element(r, err);
-        const TElem ident = telem_identity();
-        const TElem inc = warp_scan_incl<FSST>(e, lane, ident);
-        TElem lex = shfl_up_e<FSST>(inc, 1);
-        if (lane == 0) lex = ident;
-        const TElem tot = shfl_e<FSST>(inc, 31);
-
         const u64 tile_excl = ex & 0x7fffffffffffffffull;
         const u32 s_tile = FSST ? (u32)(ex >> 63) : 0u;
-        const u64 tile_incl = tile_excl + ((FSST && s_tile) ? tot.b1 : tot.b0);
-        const u32 tile_out_state = FSST ? ((tot.n >> s_tile) & 1u) : 0u;
-        const u32 s_in = FSST ? ((lex.n >> s_tile) & 1u) : 0u;
-        const u32 thr = (FSST && s_tile) ? lex.b1 : lex.b0;
-        const bool last_tile = (t == x.n_tiles - 1);
-        const bool skip = p.size_only || tile_incl > p.capacity;
 
-        Assembler as;
-        as.begin(p.out, tile_excl + thr, &area.fa[lane]);
+        // bytes of each slot (cw, one byte per slot) and of the lane; FSST-8:
+        // the lane's entering escape state first, then its literals
+        u32 cw[K / 4];
         u32 produced = 0;
+        u32 lit = 0, exit_state = 0;
         if (!FSST) {
 #pragma unroll
             for (int j = 0; j < K / 4; ++j) {
-                const u32 cw = allv ? r.L[j] : (r.L[j] & bytes_of4(r.valid >> (4 * j)));
-                area.contrib[j][lane] = cw;
-                produced += byte_sum(cw);
-            }
-            if (!skip) {
-                if (allv) assemble_onpair<true>(p, dict, r, as);
-                else assemble_onpair<false>(p, dict, r, as);
+                // a code without a token (length 0) is corrupt input
+                if (allv) {
+                    cw[j] = r.L[j];
+                    if (has_zero_byte(cw[j])) err |= ERRB_CORRUPT;
+                } else {
+                    const u32 vm = bytes_of4(r.valid >> (4 * j));
+                    cw[j] = r.L[j] & vm;
+                    if (__vcmpeq4(r.L[j], 0u) & vm) err |= ERRB_CORRUPT;
+                }
+                produced += byte_sum(cw[j]);
             }
         } else {
-            u32 lit = 0;
-            u32 cw[K / 4];
+            const u32 E = allv ? ff_mask(r) : 0u;
+            u32 x0;
+            bool ident;
+            lane_state(r, allv, E, x0, ident);
+            const u32 s_in = enter_state(__ballot_sync(0xffffffffu, !ident), x0, s_tile, lane);
+            exit_state = ident ? s_in : x0;
             if (allv) {
                 u32 esc;
-                fsst_escapes<K>(ff_mask(r), s_in, lit, esc);
+                fsst_escapes<K>(E, s_in, lit, esc);
                 const u32 code_slots = ~(lit | esc) & full_mask();
 #pragma unroll
                 for (int j = 0; j < K / 4; ++j) {
@@ -501,15 +544,44 @@ struct WarpCore {
                     produced += a;
                 }
             }
-#pragma unroll
-            for (int j = 0; j < K / 4; ++j) area.contrib[j][lane] = cw[j];
             area.lit_mask[lane] = lit;
-            if (!skip) {
+        }
+
+        // the lane's output offset in the tile: one warp scan of byte counts
+        u32 inc = produced;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= (u32)d) inc += y;
+        }
+        const u32 thr = inc - produced;
+        const u32 tot = __shfl_sync(0xffffffffu, inc, 31);
+        const u64 tile_incl = tile_excl + tot;
+        const u32 tile_out_state = FSST ? __shfl_sync(0xffffffffu, exit_state, 31) : 0u;
+        const bool last_tile = (t == x.n_tiles - 1);
+        const bool skip = p.size_only || tile_incl > p.capacity;
+
+        // per-slot bytes and the offsets of every fourth slot, for the string offsets
+        {
+            u32 o = thr;
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                area.contrib[j][lane] = cw[j];
+                area.pre[j][lane] = o;
+                o += byte_sum(cw[j]);
+            }
+        }
+        Assembler as;
+        as.begin(p.out, tile_excl + thr, &area.fa[lane]);
+        if (!skip) {
+            if (!FSST) {
+                if (allv) assemble_onpair<true>(p, dict, r, as);
+                else assemble_onpair<false>(p, dict, r, as);
+            } else {
                 if (allv) assemble_fsst<true>(p, dict, r, cw, lit, as);
                 else assemble_fsst<false>(p, dict, r, cw, lit, as);
             }
         }
-        area.thr_excl[lane] = thr;
         as.finish(produced > 0u && !skip);
         area.meta[lane] = as.meta;
         __syncwarp();
@@ -520,11 +592,11 @@ struct WarpCore {
         Partial pd;
         pd.pending = false;
         if (wrote && (as.meta & FB_VALID))
-            combine_lanes(as.g, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
+            combine_lanes(as.g(), as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
         store_partials(pd);
         pd.pending = false;
         if (wrote && (as.meta & FA_VALID) && thr == 0u)
-            combine_lanes(as.dst0, area.fa[lane], (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
+            combine_lanes(as.dst0(), area.fa[lane], (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
                           (int)lane + 1, area.fa, area.meta, pd);
         store_partials(pd);
 
@@ -552,16 +624,8 @@ struct WarpCore {
             } else {
                 const u32 sidx = (u32)(pos - tile_start);
                 const u32 j = sidx / K, k = sidx % K;
-                u32 acc = area.thr_excl[j];
-#pragma unroll
-                for (int m = 0; m < K / 4; ++m) {
-                    const u32 w = area.contrib[m][j];
-                    u32 keep = 0u;
-                    if ((u32)m < k / 4) keep = 0xffffffffu;
-                    else if ((u32)m == k / 4 && (k & 3u)) keep = 0xffffffffu >> (32 - 8 * (k & 3u));
-                    acc += byte_sum(w & keep);
-                }
-                rel = acc;
+                // offset of slot k's group of four, then the group's slots before k
+                rel = area.pre[k >> 2][j] + byte_sum(area.contrib[k >> 2][j] & ((1u << (8u * (k & 3u))) - 1u));
                 if (FSST) st = (area.lit_mask[j] >> k) & 1u;
             }
             if (st) err |= ERRB_CORRUPT;   // a string would start on a literal
@@ -625,15 +689,8 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
             if (t < x.n_tiles) {
                 typename C::R r;
                 C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r);
-                const TElem e = C::element(r, err);
-                if (C::FSST) {
-                    const TElem inc = warp_scan_incl<true>(e, lane, telem_identity());
-                    if (lane == 31) agg[t] = wt_pack<true>(inc);
-                } else {
-                    // OnPair: the tile's element is its byte count, a plain warp sum
-                    const u32 sum = __reduce_add_sync(0xffffffffu, e.b0);
-                    if (lane == 31) agg[t] = sum;
-                }
+                const TElem e = C::tile_element(r, lane, err);
+                if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
             }
         }
 #pragma unroll
@@ -738,6 +795,8 @@ __global__ void __launch_bounds__(256) tiles_scan_kernel(const DecodeParams p, c
                                                          u64* ex, unsigned long long* status) {
     __shared__ ScanShared sh;
     WsHeader* ws = p.ws;
+    grid_release();   // the decode may start launching (its blocks stage the dictionary, then wait)
+    grid_wait();      // the reduce's elements and extent
     const Extent x = *xp;
     const u32 epoch = *(volatile u32*)&ws->epoch;
     const u64 n = x.n_tiles;
@@ -772,6 +831,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
         for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
         __syncthreads();
     }
+    grid_wait();   // the tile scan's offsets (the dictionary staging above overlapped it)
     const Extent x = *xp;
     const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
     WarpArea<K>& area = areas[threadIdx.x >> 5];
