@@ -48,6 +48,8 @@ def _load():
             lib.fpo_sidecar.restype = U64
             lib.fpo_decode_rows.argtypes = [I, P, P, U32, P, U64, P, U32, P, U32, P, U64, P, P, P]
             lib.fpo_decode_rows.restype = I
+            lib.fpo_decode_packed.argtypes = [I, I, P, P, U32, P, U64, P, U32, P, U64, P, P, P]
+            lib.fpo_decode_packed.restype = I
             _lib = lib
     return _lib
 
@@ -155,6 +157,28 @@ def decode_rows(codec: int, dict_data, dict_offsets, stream, code_offsets, row_i
     offs = np.zeros(m + 1, np.uint32)
     r = lib.fpo_decode_rows(codec, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), co.size - 1,
                             rp, m, _ptr(out), capacity, _ptr(offs), ctypes.byref(total), ctypes.byref(err))
+    return OracleResult(r, err.value, total.value, out[:min(total.value, capacity)], offs)
+
+
+def decode_packed(codec: int, bits: int, dict_data, dict_offsets, stream, code_offsets,
+                  capacity: int | None = None) -> OracleResult:
+    """Decode a column whose codes are bit-packed at ``bits`` bits per code
+    (LSB-first), for the escape-free codecs."""
+    lib = _load()
+    dd, do, st, st_bytes, co = _args(codec, dict_data, dict_offsets, stream, code_offsets)
+    n_strings = co.size - 1
+    total = ctypes.c_uint64(0)
+    err = ctypes.c_uint(0)
+    if capacity is None:
+        r = lib.fpo_decode_packed(codec, bits, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co),
+                                  n_strings, None, 0, None, ctypes.byref(total), ctypes.byref(err))
+        if r not in (OK, ERR_OVERFLOW):
+            return OracleResult(r, err.value, total.value, None, None)
+        capacity = total.value
+    out = np.zeros(max(capacity, 1), np.uint8)
+    offs = np.zeros(n_strings + 1, np.uint32)
+    r = lib.fpo_decode_packed(codec, bits, _ptr(dd), _ptr(do), do.size - 1, _ptr(st), st_bytes, _ptr(co), n_strings,
+                              _ptr(out), capacity, _ptr(offs), ctypes.byref(total), ctypes.byref(err))
     return OracleResult(r, err.value, total.value, out[:min(total.value, capacity)], offs)
 
 

@@ -30,6 +30,12 @@
  *
  * Every loop is the definition written out: the 12-bit reader goes bit by
  * bit, token copies go byte by byte, and nothing is over-copied.
+ *
+ * Cascaded codes (fpo_decode_packed): the paper prepares columns on the host
+ * by widening their stored, bit-packed codes (Sec. 5).  That layer is read
+ * here as codes bit-packed at a width of b bits, LSB-first: code i occupies
+ * stream bits [b i, b i + b) (b = 12 is the OnPair-12 / FSST-12 layout, b =
+ * 16 the OnPair-16 one); everything else is the codec's decode.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -78,7 +84,17 @@ typedef struct {
     const uint8_t* stream;
     uint64_t n_slots;          /* whole code slots present in the stream */
     const uint32_t* code_offsets;
+    int packed_bits;           /* 0: the codec's stored layout; else codes bit-packed at this width */
 } column_t;
+
+/* Code in slot s of a column: the codec's layout, or b-bit packing read
+ * bit by bit. */
+static uint32_t column_code(const column_t* c, uint64_t s) {
+    if (!c->packed_bits) return read_code(c->codec, c->stream, s);
+    uint32_t v = 0;
+    for (int k = 0; k < c->packed_bits; ++k) v |= read_bit(c->stream, (uint64_t)c->packed_bits * s + k) << k;
+    return v;
+}
 
 /*
  * Decode strings [s0, s1) into out (whose byte 0 corresponds to output
@@ -93,10 +109,10 @@ static uint64_t decode_range(const column_t* c, uint32_t s0, uint32_t s1, uint8_
     for (uint32_t i = s0; i < s1; ++i) {
         uint64_t j = c->code_offsets[i], end = c->code_offsets[i + 1];
         while (j < end) {
-            uint32_t code = read_code(c->codec, c->stream, j);
+            uint32_t code = column_code(c, j);
             if (c->codec == FPO_FSST8 && code == 255) {
                 if (j + 1 >= end) { *err |= FPO_BIT_CORRUPT; j += 1; continue; }
-                uint8_t lit = (uint8_t)read_code(c->codec, c->stream, j + 1);
+                uint8_t lit = (uint8_t)column_code(c, j + 1);
                 if (out && pos < cap) out[pos - base] = lit;
                 pos += 1;
                 j += 2;
@@ -333,6 +349,39 @@ int fpo_decode_rows(int codec, const uint8_t* dict_bytes, const uint32_t* dict_o
     if (out && pos > out_capacity) err |= FPO_BIT_CAPACITY;
     if (pos > 0x7fffffffull) err |= FPO_BIT_OVERFLOW;
     if (total) *total = pos;
+    if (err_bits) *err_bits = err;
+    return status_of(err);
+}
+
+
+/*
+ * Decode a column whose codes are bit-packed at `bits` bits per code (the
+ * cascade layer above; codecs without escapes: OnPair-16, OnPair-12 and
+ * FSST-12, 1 <= bits <= the codec's own width).  Arguments and result as
+ * fpo_decode.
+ */
+int fpo_decode_packed(int codec, int bits, const uint8_t* dict_bytes, const uint32_t* dict_offsets,
+                      uint32_t n_entries, const uint8_t* stream, uint64_t stream_bytes,
+                      const uint32_t* code_offsets, uint32_t n_strings, uint8_t* out, uint64_t out_capacity,
+                      uint32_t* out_offsets, uint64_t* total, unsigned* err_bits) {
+    if (codec == FPO_FSST8 || bits < 1 || bits > code_bits(codec)) return FPO_ERR_ARG;
+    column_t c = {codec, dict_bytes, dict_offsets, n_entries, stream, stream_bytes * 8 / (uint64_t)bits,
+                  code_offsets, bits};
+    unsigned err = 0;
+    int st = check_column(&c, n_strings, &err);
+    if (err_bits) *err_bits = err;
+    if (st != FPO_OK) return st;
+    uint64_t* ends = (uint64_t*)malloc(sizeof(uint64_t) * (n_strings ? n_strings : 1));
+    if (!ends) return FPO_ERR_ARG;
+    uint64_t D = decode_range(&c, 0, n_strings, out, 0, out ? out_capacity : 0, ends, &err);
+    if (out_offsets) {
+        out_offsets[0] = 0;
+        for (uint32_t i = 0; i < n_strings; ++i) out_offsets[i + 1] = (uint32_t)ends[i];
+    }
+    free(ends);
+    if (out && D > out_capacity) err |= FPO_BIT_CAPACITY;
+    if (D > 0x7fffffffull) err |= FPO_BIT_OVERFLOW;
+    if (total) *total = D;
     if (err_bits) *err_bits = err;
     return status_of(err);
 }

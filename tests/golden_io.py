@@ -75,3 +75,13 @@ def sidecar_cases(name="sidecar_small.txt"):
         elif key == "expect_sidecar":
             cur[key] = np.array([int(t) for t in rest.split()], np.uint64)
     return cases
+
+
+def packed_cases(name="packed_examples.txt"):
+    """(bits, codes, stream bytes) of the hand-packed examples."""
+    out = []
+    for ln in _lines(name):
+        head, _, rest = ln.partition(":")
+        codes_s, _, stream_s = rest.partition("->")
+        out.append((int(head), [int(t, 16) for t in codes_s.split()], _hex(stream_s)))
+    return out
