@@ -361,17 +361,17 @@ constexpr u32 FB_HI_SHIFT = 12;      // 5 bits
 // how many of its bytes are filled (including a predecessor's bytes when the
 // thread's output starts inside the chunk).  When the thread's first chunk
 // is shared with its predecessor, that chunk is stored into the thread's
-// head slot in shared memory instead of global memory.  The position is kept
-// as a 32-bit chunk index from the thread's first chunk and a flag for the
-// head slot, so an insert updates two words, not 64-bit pointers.
+// head slot in shared memory instead of global memory; `tgt` points at
+// wherever the current chunk goes, so each insert stores through one
+// pointer and needs no test of which chunk it completes.
 struct Assembler {
     u32 c[4];
     u32 f;          // filled bytes of the current chunk
     u32 f0;         // first byte of this thread in its first chunk
-    u32 gi;         // current chunk, counted from the first one
-    bool in_head;   // the current chunk is the first one and goes to the head slot
-    uint4* base;    // first chunk in global memory
-    uint4* head;    // the thread's head slot (shared memory)
+    uint4* g;       // current chunk in global memory
+    uint4* dst0;    // first chunk in global memory
+    uint4* tgt;     // where the current chunk is stored when it completes
+    uint4* head;    // the thread's head slot (shared memory, generic address)
     uint4 fb;
     u32 meta;
 
@@ -379,15 +379,13 @@ struct Assembler {
         c[0] = c[1] = c[2] = c[3] = 0u;
         f0 = (u32)(O & 15u);
         f = f0;
-        base = reinterpret_cast<uint4*>(out) + (O >> 4);
-        gi = 0u;
+        g = reinterpret_cast<uint4*>(out) + (O >> 4);
+        dst0 = g;
         head = head_slot;
-        in_head = f0 != 0u;
+        tgt = f0 != 0u ? head_slot : g;
         meta = 0u;
         fb = make_uint4(0, 0, 0, 0);
     }
-    __device__ __forceinline__ uint4* g() const { return base + gi; }   // current chunk in global memory
-    __device__ __forceinline__ uint4* dst0() const { return base; }
     // Append a token (zero padded beyond len).  When the chunk completes it is
     // stored and the token's overflow starts the next chunk.  No branches:
     // every step runs the same instructions.
@@ -397,12 +395,9 @@ struct Assembler {
         f += len;
         const bool fl = f >= 16u;
         const uint4 full = make_uint4(c[0] | s[0], c[1] | s[1], c[2] | s[2], c[3] | s[3]);
-        if (fl) {
-            if (in_head) *head = full;
-            else base[gi] = full;
-        }
-        gi += fl ? 1u : 0u;
-        in_head = in_head && !fl;
+        if (fl) *tgt = full;
+        g += fl ? 1 : 0;
+        tgt = fl ? g : tgt;
         c[0] = fl ? s[4] : full.x;
         c[1] = fl ? s[5] : full.y;
         c[2] = fl ? s[6] : full.z;
@@ -414,7 +409,7 @@ struct Assembler {
     __device__ __forceinline__ void finish(bool nonempty) {
         if (!nonempty) return;
         const bool head_shared = f0 != 0u;
-        const bool head_open = in_head;   // the first chunk is shared and never completed
+        const bool head_open = head_shared && tgt == head;   // the first chunk never completed
         if (head_shared && !head_open) meta |= FA_VALID | (f0 << FA_LO_SHIFT) | (16u << FA_HI_SHIFT);
         if (head_open) {
             if (f > f0) {
@@ -613,10 +608,12 @@ __device__ __forceinline__ u32 ff_bits4(u32 w) {
     const u32 eq = __vcmpeq4(w, 0xffffffffu) & 0x01010101u;
     return (eq * 0x01020408u) >> 24;
 }
+// 4-bit mask -> 0x01 in byte k when bit k is set.
+__device__ __forceinline__ u32 ones_of4(u32 m) { return ((m & 0xfu) * 0x00204081u) & 0x01010101u; }
 // 4-bit mask -> byte mask (byte k = 0xFF when bit k is set).
-__device__ __forceinline__ u32 bytes_of4(u32 m) {
-    return (((m & 0xfu) * 0x00204081u) & 0x01010101u) * 0xffu;
-}
+__device__ __forceinline__ u32 bytes_of4(u32 m) { return ones_of4(m) * 0xffu; }
+// acc + sum of the bytes of w whose 0x01 marker in `ones` is set.
+__device__ __forceinline__ u32 masked_byte_sum(u32 w, u32 ones, u32 acc) { return __dp4a(w, ones, acc); }
 // Does any byte of w equal zero?
 __device__ __forceinline__ bool has_zero_byte(u32 w) {
     return ((w - 0x01010101u) & ~w & 0x80808080u) != 0u;
@@ -1118,9 +1115,9 @@ struct Decoder {
         // merge chunks shared between threads
         if (!skip && produced > 0u) {
             if (as.meta & FB_VALID)
-                combine_and_store(as.g(), as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)wtid + 1, sm.fa, sm.meta);
+                combine_and_store(as.g, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)wtid + 1, sm.fa, sm.meta);
             if ((as.meta & FA_VALID) && thr == 0u)
-                combine_and_store(as.dst0(), sm.fa[wtid], (as.meta >> FA_LO_SHIFT) & 31u,
+                combine_and_store(as.dst0, sm.fa[wtid], (as.meta >> FA_LO_SHIFT) & 31u,
                                   (as.meta >> FA_HI_SHIFT) & 31u, (int)wtid + 1, sm.fa, sm.meta);
         }
 

@@ -107,7 +107,11 @@ struct WarpArea {
 // 16 reads whole 16-byte entries, 8 reads the low plane (bytes 0-7) for
 // every token and the high plane (bytes 8-15) only for longer tokens.  The
 // FSST codecs have 8-byte entries (W = 8).
-template <int CODEC, int K, bool DSMEM, int W = (CODEC == FP_ONPAIR16 || CODEC == FP_ONPAIR12) ? 16 : 8>
+// PACKED: the codes are stored bit-packed at p.packed_bits bits per code
+// (LSB-first, 1..16) instead of the codec's own layout -- the cascade layer
+// the paper removes on the host (Sec. 5), unpacked here inside the kernels.
+template <int CODEC, int K, bool DSMEM, int W = (CODEC == FP_ONPAIR16 || CODEC == FP_ONPAIR12) ? 16 : 8,
+          bool PACKED = false>
 struct WarpCore {
     static constexpr bool FSST = (CODEC == FP_FSST8);   // escape codec: two-state scan elements
     static constexpr bool TOK8 = (CODEC == FP_FSST8 || CODEC == FP_FSST12);   // 8-byte table entries
@@ -115,6 +119,10 @@ struct WarpCore {
     static constexpr int TILE = 32 * K;
     static constexpr int WBITS = (CODEC == FP_ONPAIR16) ? 16 : (W12 ? 12 : 8);
     static constexpr int LANE_BYTES = K * WBITS / 8;   // code bytes of one lane
+    // words a lane loads: its code bytes, or for packed codes the 32-bit
+    // words covering K codes of up to 16 bits at any bit offset
+    static constexpr int LANE_WORDS = PACKED ? (K * 16 + 31) / 32 + 1 : LANE_BYTES / 4;
+    static constexpr int PK_STRIDE = LANE_WORDS;   // per-lane scratch words (odd: no bank conflicts)
     // entries of the table (a staged table, or the global planes)
     static constexpr int kTable = (CODEC == FP_FSST8) ? 256 : (CODEC == FP_ONPAIR16 ? 65536 : 4096);
     static constexpr int DICT_BYTES = DSMEM ? kTable * (TOK8 ? 8 : 16) : 0;
@@ -126,6 +134,7 @@ struct WarpCore {
     static_assert(LANE_BYTES % 8 == 0, "lane code bytes are read in 8-byte words");
     static_assert(W == 16 || W == 8, "read width");
     static_assert(!TOK8 || W == 8, "FSST entries are 8 bytes");
+    static_assert(!PACKED || (!FSST && K == 16), "packed codes: escape-free codecs, 16 slots per lane");
 
     static __device__ __forceinline__ u32 full_mask() { return K == 32 ? 0xffffffffu : ((1u << K) - 1u); }
 
@@ -146,9 +155,17 @@ struct WarpCore {
         }
     }
 
-    // Raw code words of the lane (LANE_BYTES / 4 words); false if the lane's
-    // bytes run past the buffer (then load_guarded() is used).
-    static __device__ __forceinline__ bool load_fast(const DecodeParams& p, u64 q0, u32 (&wv)[LANE_BYTES / 4]) {
+    // Raw code words of the lane (LANE_WORDS words); false if they run past
+    // the buffer (then load_guarded() is used).
+    static __device__ __forceinline__ bool load_fast(const DecodeParams& p, u64 q0, u32 (&wv)[LANE_WORDS]) {
+        if (PACKED) {
+            const u64 w0 = (q0 * p.packed_bits) >> 5;   // the word holding the lane's first bit
+            if ((w0 + LANE_WORDS) * 4 > p.codes_bytes) return false;
+            const u32* src = reinterpret_cast<const u32*>(p.codes) + w0;
+#pragma unroll
+            for (int i = 0; i < LANE_WORDS; ++i) wv[i] = __ldcs(src + i);
+            return true;
+        }
         const u64 b0 = q0 * WBITS / 8;   // q0 is a multiple of K, K a multiple of 8
         if (b0 + LANE_BYTES > p.codes_bytes) return false;
         if (LANE_BYTES % 16 == 0) {
@@ -170,6 +187,28 @@ struct WarpCore {
     }
 
     static __device__ void load_guarded(const DecodeParams& p, u64 q0, R& r) {
+        if (PACKED) {
+            // bit-packed codes near the end of the buffer: byte by byte
+            const u32 b = p.packed_bits, mask = (1u << b) - 1u;
+#pragma unroll
+            for (int m = 0; m < K / 2; ++m) {
+                u32 v = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const u64 q = q0 + 2 * m + h;
+                    if (q < p.max_slots) {
+                        const u64 P = q * b, by = P >> 3;
+                        u32 x = 0;
+#pragma unroll
+                        for (int e = 0; e < 3; ++e)
+                            if (by + e < p.codes_bytes) x |= (u32)p.codes[by + e] << (8 * e);
+                        v |= ((x >> (P & 7u)) & mask) << (16 * h);
+                    }
+                }
+                r.c[m] = v;
+            }
+            return;
+        }
         if (CODEC == FP_ONPAIR16) {
 #pragma unroll
             for (int m = 0; m < K / 2; ++m) {
@@ -211,13 +250,39 @@ struct WarpCore {
         }
     }
 
+    // Packed codes: the lane's words go to its shared-memory scratch `pk`
+    // (a run-time bit offset cannot index registers), then each code is one
+    // funnel shift of the two words that hold it.
+    static __device__ __forceinline__ void unpack_packed(const u32 (&wv)[LANE_WORDS], u32 o, u32 b, u32* pk, R& r) {
+#pragma unroll
+        for (int i = 0; i < LANE_WORDS; ++i) pk[i] = wv[i];
+        const u32 mask = (1u << b) - 1u;
+#pragma unroll
+        for (int m = 0; m < K / 2; ++m) {
+            u32 v = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const u32 P = o + (u32)(2 * m + h) * b;   // < 32 + 15 * 16
+                const u32 i = P >> 5;
+                const u32 lo = pk[i], hi = pk[i < (u32)LANE_WORDS - 1 ? i + 1 : i];
+                v |= (__funnelshift_r(lo, hi, P) & mask) << (16 * h);
+            }
+            r.c[m] = v;
+        }
+    }
+
     // Codes (from words load_fast() fetched, or guarded loads), the slots
-    // inside the column and their token lengths.
+    // inside the column and their token lengths.  `pk`: the lane's scratch
+    // (packed codes only).
     static __device__ __forceinline__ void finish_load(const DecodeParams& p, const Extent& x, u64 q0,
-                                                       const u32 (&wv)[LANE_BYTES / 4], bool fast, const uint8_t* lens,
-                                                       R& r) {
-        if (fast) unpack_words(wv, r);
-        else load_guarded(p, q0, r);
+                                                       const u32 (&wv)[LANE_WORDS], bool fast, const uint8_t* lens,
+                                                       R& r, u32* pk = nullptr) {
+        if (fast) {
+            if (PACKED) unpack_packed(wv, (u32)((q0 * p.packed_bits) & 31u), p.packed_bits, pk, r);
+            else unpack_words(wv, r);
+        } else {
+            load_guarded(p, q0, r);
+        }
         if (q0 >= x.c_begin && q0 + K <= x.c_end) {
             r.valid = full_mask();
         } else {
@@ -252,7 +317,7 @@ struct WarpCore {
     static __device__ __forceinline__ u32 fsst_bytes(const R& r, u32 codes, u32 lits) {
         u32 n = __popc(lits);
 #pragma unroll
-        for (int j = 0; j < K / 4; ++j) n += byte_sum(r.L[j] & bytes_of4(codes >> (4 * j)));
+        for (int j = 0; j < K / 4; ++j) n = masked_byte_sum(r.L[j], ones_of4(codes >> (4 * j)), n);
         return n;
     }
 
@@ -427,7 +492,7 @@ struct WarpCore {
     // the first PB*32 of their code_offsets (one per lane and round).
     static constexpr int PB = FSST ? 2 : 1;
     struct Fetch {
-        u32 wv[LANE_BYTES / 4];
+        u32 wv[LANE_WORDS];
         bool fast;
         u64 ex;
         u32 lo, hi;
@@ -468,7 +533,7 @@ struct WarpCore {
     // per tile).
     static __device__ __forceinline__ void decode_tile(const DecodeParams& p, const Extent& x, u64 t, const Fetch& f,
                                                        const u64* ex_tiles, const uint4* dict, const uint8_t* lens,
-                                                       WarpArea<K>& area, u32& err) {
+                                                       WarpArea<K>& area, u32& err, u32* pk = nullptr) {
         const u32 lane = threadIdx.x & 31u;
         const u64 tile_start = (x.first_tile + t) * (u64)TILE;
         const u64 q0 = tile_start + (u64)lane * K;
@@ -477,7 +542,7 @@ struct WarpCore {
         const bool chk = lane == 0u && t + 1 < x.n_tiles;
         const u32 ex_next = chk ? __ldg(reinterpret_cast<const u32*>(ex_tiles + t + 1)) : 0u;
         R r;
-        finish_load(p, x, q0, f.wv, f.fast, lens, r);
+        finish_load(p, x, q0, f.wv, f.fast, lens, r, pk);
         r.t = (u32)t;
         r.tile_start = tile_start;
         const bool allv = (r.valid == full_mask());
@@ -516,8 +581,9 @@ struct WarpCore {
                 const u32 code_slots = ~(lit | esc) & full_mask();
 #pragma unroll
                 for (int j = 0; j < K / 4; ++j) {
-                    cw[j] = (r.L[j] & bytes_of4(code_slots >> (4 * j))) | (bytes_of4(lit >> (4 * j)) & 0x01010101u);
-                    if (has_zero_byte(r.L[j] | ~bytes_of4(code_slots >> (4 * j)))) err |= ERRB_CORRUPT;
+                    const u32 code_ff = bytes_of4(code_slots >> (4 * j));
+                    cw[j] = (r.L[j] & code_ff) | ones_of4(lit >> (4 * j));
+                    if (has_zero_byte(r.L[j] | ~code_ff)) err |= ERRB_CORRUPT;
                     produced += byte_sum(cw[j]);
                 }
             } else {
@@ -592,11 +658,11 @@ struct WarpCore {
         Partial pd;
         pd.pending = false;
         if (wrote && (as.meta & FB_VALID))
-            combine_lanes(as.g(), as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
+            combine_lanes(as.g, as.fb, 0u, (as.meta >> FB_HI_SHIFT) & 31u, (int)lane + 1, area.fa, area.meta, pd);
         store_partials(pd);
         pd.pending = false;
         if (wrote && (as.meta & FA_VALID) && thr == 0u)
-            combine_lanes(as.dst0(), area.fa[lane], (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
+            combine_lanes(as.dst0, area.fa[lane], (as.meta >> FA_LO_SHIFT) & 31u, (as.meta >> FA_HI_SHIFT) & 31u,
                           (int)lane + 1, area.fa, area.meta, pd);
         store_partials(pd);
 
@@ -642,10 +708,11 @@ struct WarpCore {
 // Blocks [0, index_blocks) run the index pass (first string of every warp
 // tile; block 0 also stores the column's extent for the later passes), the
 // others the reduce: the two overlap in one launch.
-template <int CODEC, int K, bool DSMEM>
+template <int CODEC, int K, bool DSMEM, bool PACKED = false>
 __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Extent* xp, u64* agg, u32 index_blocks) {
-    typedef WarpCore<CODEC, K, DSMEM> C;
+    typedef WarpCore<CODEC, K, DSMEM, WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16, PACKED> C;
     __shared__ __align__(16) uint8_t s_lens[DSMEM ? C::LENS_BYTES : 16];
+    __shared__ u32 s_pk[PACKED ? 256 * C::PK_STRIDE : 1];   // packed codes: per-lane scratch
     if (blockIdx.x < index_blocks) {
         const Extent x = column_extent(p, C::TILE);
         if (blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
@@ -668,7 +735,7 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
     // rounds of U tiles; the next round's loads are in flight while this one computes
     constexpr int U = 2;
     u64 t0 = (u64)rblock * (blockDim.x / 32) + (threadIdx.x >> 5);
-    u32 wv[U][C::LANE_BYTES / 4];
+    u32 wv[U][C::LANE_WORDS];
     bool fast[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -676,7 +743,7 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
         fast[u] = t < x.n_tiles && C::load_fast(p, C::lane_q0(x, t), wv[u]);
     }
     for (; t0 < x.n_tiles; t0 += U * warps) {
-        u32 nv[U][C::LANE_BYTES / 4];
+        u32 nv[U][C::LANE_WORDS];
         bool nfast[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -688,7 +755,7 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
             const u64 t = t0 + u * warps;
             if (t < x.n_tiles) {
                 typename C::R r;
-                C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r);
+                C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r, s_pk + threadIdx.x * C::PK_STRIDE);
                 const TElem e = C::tile_element(r, lane, err);
                 if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
             }
@@ -696,7 +763,7 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
 #pragma unroll
         for (int u = 0; u < U; ++u) {
 #pragma unroll
-            for (int i = 0; i < C::LANE_BYTES / 4; ++i) wv[u][i] = nv[u][i];
+            for (int i = 0; i < C::LANE_WORDS; ++i) wv[u][i] = nv[u][i];
             fast[u] = nfast[u];
         }
     }
@@ -814,14 +881,17 @@ __global__ void __launch_bounds__(256) tiles_scan_kernel(const DecodeParams p, c
 // ---------------------------------------------------------------------------
 // Pass 3: every warp decodes warp tiles on its own (grid-stride order).
 // ---------------------------------------------------------------------------
-template <int CODEC, int K, bool DSMEM, int NW, int MINB, int W = WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16>
+template <int CODEC, int K, bool DSMEM, int NW, int MINB, int W = WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16,
+          bool PACKED = false>
 __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const DecodeParams p, const Extent* xp,
                                                                      const u64* ex) {
-    typedef WarpCore<CODEC, K, DSMEM, W> C;
+    typedef WarpCore<CODEC, K, DSMEM, W, PACKED> C;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint4* s_dict = reinterpret_cast<uint4*>(smem_raw);
     uint8_t* s_lens = smem_raw + C::DICT_BYTES;
     WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
+    // packed codes: a scratch of PK_STRIDE words per lane after the warp areas
+    u32* pk = PACKED ? reinterpret_cast<u32*>(areas + NW) + threadIdx.x * C::PK_STRIDE : nullptr;
     if (DSMEM) {
         // FSST: the 8-byte entries as they are; OnPair: the two planes (entry
         // e's bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e)
@@ -852,7 +922,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
             u32 lo2 = 0, hi2 = 0;
             if (tn < x.n_tiles) C::fetch(p, x, ex, tn, lo1, hi1, nxt);
             if (t2 < x.n_tiles) C::bounds(p, t2, lo2, hi2);
-            C::decode_tile(p, x, t, cur, ex, s_dict, lens, area, err);
+            C::decode_tile(p, x, t, cur, ex, s_dict, lens, area, err, pk);
             cur = nxt;
             lo1 = lo2;
             hi1 = hi2;
