@@ -219,6 +219,30 @@ fp_status fp_decode_rows(fp_codec codec, const fp_dict* dict, const void* d_code
                          uint32_t* d_out_offsets, fp_stream_t stream);
 
 /*
+ * Cascaded codes (paper Sec. 2.1 and Sec. 5: FSST-family codes are integers
+ * that lightweight numeric encodings compress further, and the paper widens
+ * the stored, bit-packed codes on the host before it decodes).  These calls
+ * decode a column whose codes are bit-packed at code_bits bits per code
+ * (LSB-first: code i occupies stream bits [code_bits i, code_bits i +
+ * code_bits), stream bit k is bit (k mod 8) of byte k / 8), unpacking them
+ * inside the decode's own kernels -- no widened copy is made.  Typically
+ * code_bits = ceil(log2(n_entries)) of the dictionary.
+ *
+ *   codec       FP_ONPAIR16, FP_ONPAIR12 or FP_FSST12 (escape-free codecs).
+ *   code_bits   1 .. the codec's own width (16, 12, 12); at the codec's own
+ *               width the layout is the codec's stored layout.
+ *   d_codes     16-byte aligned; slots are the whole codes in codes_bytes.
+ * Everything else (arguments, output, errors, workspace) as fp_decode /
+ * fp_decoded_size; FP_ERR_ARG for another codec or width.
+ */
+fp_status fp_decode_packed(fp_codec codec, const fp_dict* dict, uint32_t code_bits, const void* d_codes,
+                           uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                           uint8_t* d_out_bytes, uint64_t out_capacity, uint32_t* d_out_offsets, fp_stream_t stream);
+fp_status fp_decoded_size_packed(fp_codec codec, const fp_dict* dict, uint32_t code_bits, const void* d_codes,
+                                 uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                                 fp_stream_t stream, uint64_t* h_total);
+
+/*
  * fp_decode_plain -- baseline decoder with one thread per string.
  *
  * Same arguments, result and error behaviour as fp_decode.  Each thread

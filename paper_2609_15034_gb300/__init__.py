@@ -62,6 +62,8 @@ def lib() -> ctypes.CDLL:
             L.fp_debug_stall_next.argtypes = [P, U32]
             L.fp_rows_size.argtypes = [I, P, P, U64, P, U32, P, U32, P, ctypes.POINTER(U64), ctypes.POINTER(U64)]
             L.fp_decode_rows.argtypes = [I, P, P, U64, P, U32, P, U32, U64, P, U64, P, P]
+            L.fp_decode_packed.argtypes = [I, P, U32, P, U64, P, U32, P, U64, P, P]
+            L.fp_decoded_size_packed.argtypes = [I, P, U32, P, U64, P, U32, P, ctypes.POINTER(U64)]
             L.fp_last_error.restype = ctypes.c_char_p
             L.fp_variant_count.argtypes = [I]
             L.fp_variant_info.argtypes = [I, I, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32),
@@ -99,7 +101,8 @@ def lib() -> ctypes.CDLL:
             for name in ("fp_dict_upload", "fp_dict_free", "fp_decode", "fp_decode_plain", "fp_decoded_size",
                          "fp_decode_noalloc",
                          "fp_sync_status", "fp_debug_stall_next", "fp_variant_info", "fp_variant_select",
-                         "fp_dict_set_width", "fp_rows_size", "fp_decode_rows",
+                         "fp_dict_set_width", "fp_rows_size", "fp_decode_rows", "fp_decode_packed",
+                         "fp_decoded_size_packed",
                          "fp_plan_create", "fp_plan_create_config", "fp_decode_batch", "fp_plan_sync_status",
                          "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info", "fp_serve_create",
                          "fp_serve_dict_put", "fp_serve_submit", "fp_serve_poll", "fp_serve_release",
@@ -344,6 +347,24 @@ def decode_rows(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_p
     st = lib().fp_decode_rows(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, row_ids_ptr,
                               n_rows, selected_slots, out_ptr, capacity, out_offsets_ptr, _stream(stream))
     return _check(st, "fp_decode_rows") if check else st
+
+
+def decode_packed(codec, d: Dict, code_bits: int, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int,
+                  n_strings: int, out_ptr: int, capacity: int, out_offsets_ptr: int, stream=None,
+                  check: bool = True) -> int:
+    """fp_decode_packed: decode a column whose codes are bit-packed at code_bits bits."""
+    st = lib().fp_decode_packed(codec, d.handle, code_bits, codes_ptr, codes_bytes, code_offsets_ptr, n_strings,
+                                out_ptr, capacity, out_offsets_ptr, _stream(stream))
+    return _check(st, "fp_decode_packed") if check else st
+
+
+def decoded_size_packed(codec, d: Dict, code_bits: int, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int,
+                        n_strings: int, stream=None):
+    """fp_decoded_size_packed: (status, decoded bytes).  Synchronous."""
+    tot = ctypes.c_uint64(0)
+    st = lib().fp_decoded_size_packed(codec, d.handle, code_bits, codes_ptr, codes_bytes, code_offsets_ptr,
+                                      n_strings, _stream(stream), ctypes.byref(tot))
+    return st, int(tot.value)
 
 
 def debug_stall_next(spin_limit: int, stream=None) -> int:

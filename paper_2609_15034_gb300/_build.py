@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfastpair.so")
 
 SOURCES = ["fp_api.cu", "fp_decode.cu", "fp_var16.cu", "fp_var12.cu", "fp_var8.cu", "fp_var12f.cu", "fp_batch.cu",
-           "fp_plain.cu", "fp_serve.cu", "fp_sidecar.cu", "fp_rows.cu"]
+           "fp_plain.cu", "fp_serve.cu", "fp_sidecar.cu", "fp_rows.cu",
+           "fp_varpk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--cudart", "shared",
               "-Xptxas", "-v", "-I", INCLUDE, "-I", CSRC]
@@ -36,7 +37,7 @@ def nvcc() -> str:
 # Sources of the single-column decode (fp_decode and its kernels): DRAM
 # traffic counters taken on one build stay valid while these and the build
 # flags are unchanged.
-DECODE_PATH = ["fp_api.cu", "fp_decode.cu", "fp_var16.cu", "fp_var12.cu", "fp_var8.cu", "fp_var12f.cu",
+DECODE_PATH = ["fp_api.cu", "fp_decode.cu", "fp_var16.cu", "fp_var12.cu", "fp_var8.cu", "fp_var12f.cu", "fp_varpk.cu",
                "fp_variants.cuh", "fp_decoder.cuh", "fp_internal.h", "fp_warp.cuh"]
 
 

@@ -215,9 +215,10 @@ fp_status take_status(Workspace* w, uint64_t* total, cudaStream_t stream) {
 fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
                      const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
                      uint64_t out_capacity, uint32_t* d_out_offsets, cudaStream_t stream, bool size_only,
-                     Workspace** ws_out) {
-    const uint64_t max_slots = max_slots_of(codec, codes_bytes);
-    const Variant* var = variant_get(codec, selected_variant(codec, max_slots, dict->width));
+                     Workspace** ws_out, uint32_t packed_bits = 0) {
+    const uint64_t max_slots = packed_bits ? codes_bytes * 8 / packed_bits : max_slots_of(codec, codes_bytes);
+    const Variant* var = packed_bits ? variant_packed(codec)
+                                     : variant_get(codec, selected_variant(codec, max_slots, dict->width));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
     const uint64_t tile = variant_tile(*var);
@@ -246,6 +247,7 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
     p.out_offsets = d_out_offsets;
     p.ws = static_cast<WsHeader*>(w->d_mem);
     p.size_only = size_only ? 1 : 0;
+    p.packed_bits = packed_bits;
     const uint64_t grid = (n_tiles < (uint64_t)per_wave && !var->warp_tiles) ? n_tiles : (uint64_t)per_wave;
     cudaError_t e = launch_decode(codec, *var, p, static_cast<char*>(w->d_mem) + kWsHeaderBytes, max_slots,
                                   (int)grid, sms, stream);
@@ -470,6 +472,46 @@ fp_status fp_decode_rows(fp_codec codec, const fp_dict* dict, const void* d_code
     if (st != FP_OK) return st;
     return run_rows(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_row_ids, n_rows, selected_slots,
                     d_out_bytes, out_capacity, d_out_offsets, reinterpret_cast<cudaStream_t>(stream), false, nullptr);
+}
+
+namespace {
+fp_status check_packed(fp_codec codec, uint32_t code_bits_) {
+    if (codec != FP_ONPAIR16 && codec != FP_ONPAIR12 && codec != FP_FSST12)
+        return fail(FP_ERR_ARG, "packed codes: codec %d has escapes or is unknown", (int)codec);
+    if (code_bits_ < 1 || code_bits_ > code_bits(codec))
+        return fail(FP_ERR_ARG, "packed codes: %u bits per code, the codec allows 1..%u", code_bits_, code_bits(codec));
+    return FP_OK;
+}
+}  // namespace
+
+fp_status fp_decode_packed(fp_codec codec, const fp_dict* dict, uint32_t code_bits_, const void* d_codes,
+                           uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                           uint8_t* d_out_bytes, uint64_t out_capacity, uint32_t* d_out_offsets, fp_stream_t stream) {
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, d_out_bytes, out_capacity,
+                                d_out_offsets, true);
+    if (st == FP_OK) st = check_packed(codec, code_bits_);
+    if (st != FP_OK) return st;
+    if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
+    return run_decode(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_out_bytes, out_capacity,
+                      d_out_offsets, reinterpret_cast<cudaStream_t>(stream), false, nullptr, code_bits_);
+}
+
+fp_status fp_decoded_size_packed(fp_codec codec, const fp_dict* dict, uint32_t code_bits_, const void* d_codes,
+                                 uint64_t codes_bytes, const uint32_t* d_code_offsets, uint32_t n_strings,
+                                 fp_stream_t stream_, uint64_t* h_total) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!h_total) return fail(FP_ERR_ARG, "h_total is NULL");
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, nullptr, 0, nullptr, false);
+    if (st == FP_OK) st = check_packed(codec, code_bits_);
+    if (st != FP_OK) return st;
+    if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
+    Workspace* w = nullptr;
+    st = run_decode(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, nullptr, 0, nullptr, stream, true,
+                    &w, code_bits_);
+    if (st != FP_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return take_status(w, h_total, stream);
 }
 
 int fp_width_for_histogram(const uint64_t* hist17) { return hist17 ? width_for_histogram(hist17) : 8; }

@@ -99,11 +99,11 @@ __device__ __forceinline__ void reduce_queue(const BatchParams& bp, int q, u64 t
     // stall the warp once per tile.
     const SlotSrc* rc = Q.src + __ldg(Q.tile_chunk + t);
     u64 q0 = C::lane_q0(rc->x, t - rc->tile_base);
-    u32 wv[C::LANE_BYTES / 4];
+    u32 wv[C::LANE_WORDS];
     bool fast = C::load_fast(rc->p, q0, wv);
     const SlotSrc* rn = t + W < t_end ? Q.src + __ldg(Q.tile_chunk + t + W) : nullptr;
     for (; t < t_end; t += W) {
-        u32 nv[C::LANE_BYTES / 4];
+        u32 nv[C::LANE_WORDS];
         bool nfast = false;
         u64 nq0 = 0;
         if (rn) {
@@ -125,7 +125,7 @@ __device__ __forceinline__ void reduce_queue(const BatchParams& bp, int q, u64 t
         q0 = nq0;
         fast = nfast;
 #pragma unroll
-        for (int i = 0; i < C::LANE_BYTES / 4; ++i) wv[i] = nv[i];
+        for (int i = 0; i < C::LANE_WORDS; ++i) wv[i] = nv[i];
     }
 }
 

@@ -68,6 +68,8 @@ struct DecodeParams {
     unsigned int* err_word;           // where this column's data-error bits go
     unsigned long long* total_out;    // where this column's decoded size goes
     const uint32_t* first;            // tile -> first string boundary it owns (index pass)
+    uint32_t packed_bits;             // cascaded codes: bits per code (packed decode only; else 0)
+    uint32_t pad_;
 };
 
 // Tiles of a column: a tile is `tile` consecutive code slots, tile u covers
@@ -142,6 +144,9 @@ const Variant* variant_get(int codec, int v);
 // Default for a code buffer of max_slots slots and a dictionary read width
 // (8 or 16; only the OnPair codecs have both).
 int variant_default(int codec, uint64_t max_slots, int width);
+// The decoder of codes bit-packed at a run-time width (fp_decode_packed):
+// one warp-tile variant per escape-free codec, null for FSST-8.
+const Variant* variant_packed(int codec);
 // The variant fp_decode_noalloc uses when none is selected: the block
 // pipeline where the codec has one (its scratch covers the largest inputs).
 int noalloc_default(int codec);

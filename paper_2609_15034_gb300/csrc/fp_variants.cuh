@@ -44,5 +44,25 @@ Variant make_warp_variant() {
     return v;
 }
 
+// Packed codes (run-time width): the warp-tile decoder with a per-lane
+// shared-memory scratch for the code words.
+template <int CODEC, bool DSMEM, int NW>
+Variant make_packed_variant() {
+    constexpr int K = 16, W = (CODEC == FP_FSST12) ? 8 : 16;
+    typedef WarpCore<CODEC, K, DSMEM, W, true> C;
+    Variant v{};
+    v.threads = NW * 32;
+    v.slots_per_thread = K;
+    v.dict_smem = DSMEM ? 1 : 0;
+    v.smem_bytes = (size_t)C::DICT_BYTES + (DSMEM ? (size_t)C::LENS_BYTES : 0) + NW * sizeof(WarpArea<K>) +
+                   (size_t)NW * 32 * C::PK_STRIDE * sizeof(u32);
+    v.kernel = (const void*)&warp_decode_kernel<CODEC, K, DSMEM, NW, 1, W, true>;
+    v.warp_tiles = 1;
+    v.reduce = (const void*)&reduce_kernel<CODEC, K, DSMEM, true>;
+    v.scan = (const void*)&tiles_scan_kernel<false>;
+    v.width = W;
+    return v;
+}
+
 }  // namespace
 }  // namespace fp
