@@ -36,7 +36,12 @@ WORKLOADS = {
     "fsst12_16m": (synth.FSST12, 16_000_000,
                    "FSST-12 (escape-free 12-bit codes), 4,096 URL/identifier symbols of 1-8 B, 16M lognormal "
                    "strings (median 40 B), Zipf(1.0)"),
+    "fsst12_packed10_16m": (synth.FSST12, 16_000_000,
+                            "FSST-12 with a 1,024-symbol table, codes cascaded: bit-packed at 10 bits and "
+                            "unpacked inside the decode (fp_decode_packed); 16M lognormal strings (median 40 B)"),
 }
+# cascaded workloads: name -> (bits per stored code, dictionary entries)
+PACKED_WORKLOADS = {"fsst12_packed10_16m": (10, 1024)}
 # batched workloads: name -> (chunks, smallest and largest decoded chunk size, description)
 BATCH_WORKLOADS = {
     "batched_4096": (4096, 4 << 10, 64 << 20,
@@ -80,12 +85,13 @@ def env_rank():
     return r, w, lr
 
 
-def algorithmic_bytes(col, total: int, codec: int) -> int:
-    """Bytes a decode must move at least: the code slots it reads, the string
-    offsets it reads and writes, the output it writes, the dictionary once."""
+def algorithmic_bytes(col, total: int, codec: int, bits: int = 0) -> int:
+    """Bytes a decode must move at least: the code slots it reads (at `bits`
+    bits per code when they are stored bit-packed), the string offsets it
+    reads and writes, the output it writes, the dictionary once."""
     co = col.code_offsets
     used_slots = int(co[-1]) - int(co[0])
-    code_bytes = (used_slots * synth.CODE_BITS[codec] + 7) // 8
+    code_bytes = (used_slots * (bits or synth.CODE_BITS[codec]) + 7) // 8
     n = col.n_strings
     dict_bytes = col.dictionary.n_entries * (synth.MAX_TOKEN[codec] + 1)
     return code_bytes + 4 * (n + 1) + total + 4 * (n + 1) + dict_bytes
@@ -161,24 +167,43 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(col, target_s: float, threads: int):
-    """Time the oracle (as it stands) on a bounded prefix of the column."""
+def workload_column(name: str, seed: int):
+    """The workload's column and, for cascaded workloads, its bits per stored code."""
+    codec, n, _ = WORKLOADS[name]
+    if name in PACKED_WORKLOADS:
+        bits, n_entries = PACKED_WORKLOADS[name]
+        col = synth.fsst12_column(seed, n, dictionary=synth.fsst12_dictionary(seed, n_entries))
+        # the stored codes, cascaded: bit-packed at `bits` bits
+        return synth.Column(codec, col.dictionary, synth.pack_bits(col.slot_codes, bits), col.code_offsets,
+                            col.n_slots, name=col.name), bits
+    return synth.column(codec, seed, n), 0
+
+
+def cpu_oracle_rate(col, target_s: float, threads: int, packed_bits: int = 0):
+    """Time the oracle (as it stands) on a bounded prefix of the column (the
+    oracle's decode of bit-packed codes runs on one thread)."""
     import oracle
     n = col.n_strings
     # size the sample from a short probe
     probe_n = min(n, 20000)
     co = col.code_offsets
+
+    def dec(m):
+        if packed_bits:
+            return oracle.decode_packed(col.codec, packed_bits, col.dictionary.data, col.dictionary.offsets,
+                                        col.stream, co[:m + 1])
+        return oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, co[:m + 1],
+                             threads=threads)
+
     t0 = time.perf_counter()
-    r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, co[:probe_n + 1],
-                      threads=threads)
+    r = dec(probe_n)
     dt = max(time.perf_counter() - t0, 1e-4)
     rate = r.total / dt
     want_bytes = rate * target_s
     per_string = max(r.total / max(probe_n, 1), 1.0)
     m = int(min(n, max(probe_n, want_bytes / per_string)))
     t0 = time.perf_counter()
-    r = oracle.decode(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, co[:m + 1],
-                      threads=threads)
+    r = dec(m)
     dt = time.perf_counter() - t0
     return r.total / dt / 1e9, m, r.total, dt
 
@@ -187,12 +212,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     codec, n, desc = WORKLOADS[args.workload]
-    col = synth.column(codec, 0, n)
-    threads = os.cpu_count() or 1
+    col, packed_bits = workload_column(args.workload, 0)
+    threads = 1 if packed_bits else (os.cpu_count() or 1)
     vals, samples = [], []
     per_step = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
     for i in range(args.warmup + args.steps):
-        gbs, m, total, dt = cpu_oracle_rate(col, per_step, threads)
+        gbs, m, total, dt = cpu_oracle_rate(col, per_step, threads, packed_bits)
         if i >= args.warmup:
             vals.append(gbs)
             samples.append((m, total, dt))
@@ -224,7 +249,7 @@ def run_ours(args, rank, world, local_rank):
     codec, n, desc = WORKLOADS[args.workload]
     if args.n_strings:
         n = args.n_strings
-    col = synth.column(codec, rank, n)   # one independent replica column per rank
+    col, packed_bits = workload_column(args.workload, rank)   # one independent replica column per rank
     fp.variant_select(codec, args.variant)
 
     stream = torch.cuda.current_stream()
@@ -234,7 +259,11 @@ def run_ours(args, rank, world, local_rank):
         d.set_width(args.width)
     codes = torch.from_numpy(col.stream).to(dev)
     co = torch.from_numpy(col.code_offsets.view(np.int32)).to(dev)
-    st, total = fp.decoded_size_tensors(codec, d, codes, co, n, sh)
+    if packed_bits:
+        st, total = fp.decoded_size_packed(codec, d, packed_bits, codes.data_ptr(), codes.numel(), co.data_ptr(), n,
+                                           sh)
+    else:
+        st, total = fp.decoded_size_tensors(codec, d, codes, co, n, sh)
     if st != fp.OK:
         raise RuntimeError(f"decoded_size: {fp.STATUS_NAMES[st]} {fp.last_error()}")
     out = torch.empty(total, dtype=torch.uint8, device=dev)
@@ -249,12 +278,17 @@ def run_ours(args, rank, world, local_rank):
         if sidecar.status_bits() != 0:
             raise RuntimeError(f"sidecar build: data-error bits {sidecar.status_bits()}")
 
+    def decode_call(codes_ptr, co_ptr, out_ptr, offs_ptr, stream):
+        if packed_bits:
+            fp.decode_packed(codec, d, packed_bits, codes_ptr, codes_bytes, co_ptr, n, out_ptr, total, offs_ptr, stream)
+        else:
+            fp.decode(codec, d, codes_ptr, codes_bytes, co_ptr, n, out_ptr, total, offs_ptr, stream)
+
     def step():
         if sidecar is not None:
             sidecar.decode(out, offs, sh)
         else:
-            fp.decode(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
-                      offs.data_ptr(), sh)
+            decode_call(codes.data_ptr(), co.data_ptr(), out.data_ptr(), offs.data_ptr(), sh)
 
     def status_ok():
         if sidecar is not None:
@@ -308,28 +342,30 @@ def run_ours(args, rank, world, local_rank):
 
     value = all_bytes * args.steps / (total_ms * 1e-3) / 1e9
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
-    alg = algorithmic_bytes(col, total, codec)
+    alg = algorithmic_bytes(col, total, codec, packed_bits)
     peak, peak_kind = load_peaks()
     achieved = alg / avg_launch_s / 1e9
 
     extra = {}
     if rank == 0 and not args.quick:
-        # plain one-thread-per-string GPU decode, same column, same clock
-        plain_ms = []
-        for i in range(3 + args.plain_steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fp.decode_plain(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
-                            offs.data_ptr(), sh)
-            b.record(stream)
-            torch.cuda.synchronize()
-            if i >= 3:
-                plain_ms.append(a.elapsed_time(b))
-        if fp.sync_status(sh) != fp.OK:
-            raise RuntimeError(fp.last_error())
-        plain_gbs = total / (statistics.mean(plain_ms) * 1e-3) / 1e9
-        extra["plain_gpu"] = {"value": round(plain_gbs, 2), "unit": "GB/s", "kind": "one thread per string",
-                              "ms": round(statistics.mean(plain_ms), 3)}
+        # plain one-thread-per-string GPU decode, same column, same clock (it
+        # reads the codec's own layout, so not for cascaded codes)
+        if not packed_bits:
+            plain_ms = []
+            for i in range(3 + args.plain_steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fp.decode_plain(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, out.data_ptr(), total,
+                                offs.data_ptr(), sh)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if i >= 3:
+                    plain_ms.append(a.elapsed_time(b))
+            if fp.sync_status(sh) != fp.OK:
+                raise RuntimeError(fp.last_error())
+            plain_gbs = total / (statistics.mean(plain_ms) * 1e-3) / 1e9
+            extra["plain_gpu"] = {"value": round(plain_gbs, 2), "unit": "GB/s", "kind": "one thread per string",
+                                  "ms": round(statistics.mean(plain_ms), 3)}
 
         # End to end through the public API with host buffers (pinned): every
         # step copies the column's codes and code_offsets host -> device,
@@ -363,8 +399,8 @@ def run_ours(args, rank, world, local_rank):
                 s_dec.wait_event(ev_in[j])
                 if i >= 2:
                     s_dec.wait_event(ev_out[j])    # the set's outputs have been copied out
-                fp.decode(codec, d, b["codes"].data_ptr(), codes_bytes, b["co"].data_ptr(), n, b["out"].data_ptr(),
-                          total, b["offs"].data_ptr(), s_dec.cuda_stream)
+                decode_call(b["codes"].data_ptr(), b["co"].data_ptr(), b["out"].data_ptr(), b["offs"].data_ptr(),
+                            s_dec.cuda_stream)
                 ev_dec[j].record(s_dec)
                 s_out.wait_event(ev_dec[j])
                 with torch.cuda.stream(s_out):
@@ -394,8 +430,8 @@ def run_ours(args, rank, world, local_rank):
                 raise RuntimeError("end-to-end output mismatch")
 
         # CPU oracle on the host cores (reported baseline, not a target)
-        threads = os.cpu_count() or 1
-        gbs, m, tb, dt = cpu_oracle_rate(col, args.cpu_seconds, threads)
+        threads = 1 if packed_bits else (os.cpu_count() or 1)
+        gbs, m, tb, dt = cpu_oracle_rate(col, args.cpu_seconds, threads, packed_bits)
         extra["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                                  "sample": f"first {m} of {n} strings ({tb} decoded bytes), {dt:.1f} s"}
 
@@ -403,8 +439,11 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
-    var = fp.variant_for_dict(d, codes_bytes)
-    vinfo = dict(fp.variant_info(codec, var), index=var, read_width=fp.variant_width(codec, var))
+    if packed_bits:
+        vinfo = {"kind": "packed codes (fp_decode_packed)", "code_bits": packed_bits, "launches_per_call": 3}
+    else:
+        var = fp.variant_for_dict(d, codes_bytes)
+        vinfo = dict(fp.variant_info(codec, var), index=var, read_width=fp.variant_width(codec, var))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,

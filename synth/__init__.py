@@ -276,16 +276,31 @@ def fsst8_dictionary(seed: int) -> Dictionary:
     return Dictionary.from_tokens(FSST8, _url_tokens(rng, 255))
 
 
-def fsst12_dictionary(seed: int) -> Dictionary:
-    """4,096 symbols: codes 0..255 are the one-byte symbols (an escape-free
-    table must cover every byte), codes 256..4095 distinct URL/identifier-
-    like symbols of 2..8 bytes."""
-    rng = rng_for(4, seed, 0)
-    multi = [t for t in _url_tokens(rng, 6000) if len(t) >= 2][:4096 - 256]
-    while len(multi) < 4096 - 256:
+def fsst12_dictionary(seed: int, n_entries: int = 4096) -> Dictionary:
+    """n_entries symbols (257..4,096): codes 0..255 are the one-byte symbols
+    (an escape-free table must cover every byte), the rest distinct
+    URL/identifier-like symbols of 2..8 bytes."""
+    rng = rng_for(4, seed, 0, n_entries)
+    want = n_entries - 256
+    multi = [t for t in _url_tokens(rng, 6000) if len(t) >= 2][:want]
+    while len(multi) < want:
         extra = [t for t in _url_tokens(rng, 2000) if len(t) >= 2 and t not in set(multi)]
-        multi += extra[:4096 - 256 - len(multi)]
+        multi += extra[:want - len(multi)]
     return Dictionary.from_tokens(FSST12, [bytes([b]) for b in range(256)] + multi)
+
+
+def pack_bits(codes: np.ndarray, bits: int, chunk: int = 1 << 22) -> np.ndarray:
+    """Codes bit-packed at ``bits`` bits per code, LSB-first (code i at stream
+    bits [bits i, bits i + bits)): the cascaded storage of a code column,
+    written with np.packbits."""
+    codes = np.asarray(codes, np.uint32)
+    out = []
+    step = chunk - chunk % 8   # whole bytes per chunk
+    for a in range(0, codes.size, step):
+        c = codes[a:a + step]
+        b = ((c[:, None] >> np.arange(bits, dtype=np.uint32)) & 1).astype(np.uint8).reshape(-1)
+        out.append(np.packbits(b, bitorder="little"))
+    return np.concatenate(out) if out else np.zeros(0, np.uint8)
 
 
 # ---------------------------------------------------------------------------
