@@ -122,7 +122,10 @@ struct WarpCore {
     // words a lane loads: its code bytes, or for packed codes the 32-bit
     // words covering K codes of up to 16 bits at any bit offset
     static constexpr int LANE_WORDS = PACKED ? (K * 16 + 31) / 32 + 1 : LANE_BYTES / 4;
-    static constexpr int PK_STRIDE = LANE_WORDS;   // per-lane scratch words (odd: no bank conflicts)
+    // per-lane scratch: word i next to word i + 1, as 8-byte pairs; a stride
+    // of 2 * LANE_WORDS words keeps the 16 lanes of each half-warp's 8-byte
+    // accesses on distinct banks
+    static constexpr int PK_STRIDE = 2 * LANE_WORDS;
     // entries of the table (a staged table, or the global planes)
     static constexpr int kTable = (CODEC == FP_FSST8) ? 256 : (CODEC == FP_ONPAIR16 ? 65536 : 4096);
     static constexpr int DICT_BYTES = DSMEM ? kTable * (TOK8 ? 8 : 16) : 0;
@@ -254,8 +257,9 @@ struct WarpCore {
     // (a run-time bit offset cannot index registers), then each code is one
     // funnel shift of the two words that hold it.
     static __device__ __forceinline__ void unpack_packed(const u32 (&wv)[LANE_WORDS], u32 o, u32 b, u32* pk, R& r) {
+        uint2* pairs = reinterpret_cast<uint2*>(pk);
 #pragma unroll
-        for (int i = 0; i < LANE_WORDS; ++i) pk[i] = wv[i];
+        for (int i = 0; i < LANE_WORDS; ++i) pairs[i] = make_uint2(wv[i], i + 1 < LANE_WORDS ? wv[i + 1] : 0u);
         const u32 mask = (1u << b) - 1u;
 #pragma unroll
         for (int m = 0; m < K / 2; ++m) {
@@ -263,9 +267,8 @@ struct WarpCore {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const u32 P = o + (u32)(2 * m + h) * b;   // < 32 + 15 * 16
-                const u32 i = P >> 5;
-                const u32 lo = pk[i], hi = pk[i < (u32)LANE_WORDS - 1 ? i + 1 : i];
-                v |= (__funnelshift_r(lo, hi, P) & mask) << (16 * h);
+                const uint2 w = pairs[P >> 5];
+                v |= (__funnelshift_r(w.x, w.y, P) & mask) << (16 * h);
             }
             r.c[m] = v;
         }
@@ -708,11 +711,23 @@ struct WarpCore {
 // Blocks [0, index_blocks) run the index pass (first string of every warp
 // tile; block 0 also stores the column's extent for the later passes), the
 // others the reduce: the two overlap in one launch.
+// Reduce shape per codec, from an A/B on GB300 (10M-16M strings): rounds of
+// kReduceU tiles in flight, kReduceMinB blocks of 256 threads per SM.
+// OnPair-12: 2 x 4 (1,515 GB/s per call against 1,498 at 2 x 3); FSST-8,
+// whose 32-slot lanes spill at fewer than 128 registers: 2 x 2 (1,051
+// against 1,038); FSST-12: 1 x 4 (1,188 against 1,171).
+template <int CODEC, int K>
+struct ReduceShape {
+    static constexpr int U = CODEC == FP_FSST12 ? 1 : 2;
+    static constexpr int MINB = (CODEC == FP_FSST8 && K == 32) ? 2 : 4;
+};
+
 template <int CODEC, int K, bool DSMEM, bool PACKED = false>
-__global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Extent* xp, u64* agg, u32 index_blocks) {
+__global__ void __launch_bounds__(256, ReduceShape<CODEC, K>::MINB) reduce_kernel(const DecodeParams p, Extent* xp,
+                                                                                  u64* agg, u32 index_blocks) {
     typedef WarpCore<CODEC, K, DSMEM, WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16, PACKED> C;
     __shared__ __align__(16) uint8_t s_lens[DSMEM ? C::LENS_BYTES : 16];
-    __shared__ u32 s_pk[PACKED ? 256 * C::PK_STRIDE : 1];   // packed codes: per-lane scratch
+    __shared__ __align__(16) u32 s_pk[PACKED ? 256 * C::PK_STRIDE : 2];   // packed codes: per-lane scratch
     if (blockIdx.x < index_blocks) {
         const Extent x = column_extent(p, C::TILE);
         if (blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
@@ -733,7 +748,7 @@ __global__ void __launch_bounds__(256, 3) reduce_kernel(const DecodeParams p, Ex
     const u64 warps = (u64)(gridDim.x - index_blocks) * (blockDim.x / 32);
     u32 err = 0;
     // rounds of U tiles; the next round's loads are in flight while this one computes
-    constexpr int U = 2;
+    constexpr int U = ReduceShape<CODEC, K>::U;
     u64 t0 = (u64)rblock * (blockDim.x / 32) + (threadIdx.x >> 5);
     u32 wv[U][C::LANE_WORDS];
     bool fast[U];
