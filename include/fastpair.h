@@ -274,7 +274,9 @@ const char* fp_last_error(void);
  * ticketed pass (the tile scan of the warp-tile decoder, or the decode of
  * the block pipeline), so the first look-back word is never published and
  * the look-back that needs it polls it `spin_limit` times (1..2^20; the
- * built-in limit is 2^20 polls with back-off), then gives up.  The call
+ * built-in limit is 2^20 polls with back-off), then gives up; the
+ * one-launch decode's first grid barrier starts with an arrival count no
+ * grid reaches, so its blocks give up there in the same way.  The call
  * reports FP_ERR_TIMEOUT through fp_sync_status; its output is unspecified
  * but every write stays in bounds.  Both settings end with that call: the
  * next decode on the stream is normal.
@@ -523,8 +525,9 @@ fp_status fp_serve_destroy(fp_server* server);
  *                   1 if the dictionary is staged in shared memory, and the
  *                   kernel launches of one fp_decode call (2: index pass and
  *                   block-pipeline decode; 3: index pass and reduce in one
- *                   launch, tile scan, warp-tile decode).  Any out pointer
- *                   may be NULL.
+ *                   launch, tile scan, warp-tile decode; 1: the warp-tile
+ *                   passes as phases of one cooperative launch, for small
+ *                   columns).  Any out pointer may be NULL.
  * fp_variant_select make variant v the one fp_decode uses for the codec in
  *                   this process (v = -1 restores the built-in defaults,
  *                   which depend on the size of the code buffer and on the

@@ -597,11 +597,16 @@ fp_status fp_debug_stall_next(fp_stream_t stream_, uint32_t spin_limit) {
     if (!w || !w->d_mem) return fail(FP_ERR_ARG, "no workspace on this stream yet (decode once first)");
     // ticket 0 is taken here, so no launch ever publishes the first look-back
     // word; the kernels reset both fields when the launch ends
-    // (pageable sources: each copy is staged before cudaMemcpyAsync returns)
-    const unsigned skip_first = 1u, limit = spin_limit;
+    // (pageable sources: each copy is staged before cudaMemcpyAsync returns);
+    // a phantom arrival count that no grid reaches stalls the one-launch
+    // path's first grid barrier
+    const unsigned skip_first = 1u, limit = spin_limit, phantom = 1u << 30;
     char* h = static_cast<char*>(w->d_mem);
     cudaError_t e = cudaMemcpyAsync(h + offsetof(WsHeader, tile_counter), &skip_first, sizeof(unsigned),
                                     cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + offsetof(WsHeader, bar_count), &phantom, sizeof(unsigned), cudaMemcpyHostToDevice,
+                            stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h + offsetof(WsHeader, spin_limit), &limit, sizeof(unsigned), cudaMemcpyHostToDevice,
                             stream);
@@ -619,7 +624,7 @@ fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* sl
     if (threads) *threads = (uint32_t)var->threads;
     if (slots_per_thread) *slots_per_thread = (uint32_t)var->slots_per_thread;
     if (dict_in_smem) *dict_in_smem = (uint32_t)var->dict_smem;
-    if (launches_per_call) *launches_per_call = var->warp_tiles ? 3u : 2u;
+    if (launches_per_call) *launches_per_call = var->warp_tiles == 2 ? 1u : var->warp_tiles ? 3u : 2u;
     return FP_OK;
 }
 

@@ -160,13 +160,23 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
         return cudaLaunchKernel(var.kernel, dim3(grid), dim3(var.threads), args, var.smem_bytes, stream);
     }
 
+    Extent* xp = reinterpret_cast<Extent*>(base + L.o_extent);
+    u64* agg = reinterpret_cast<u64*>(base + L.o_agg);
+    u64* ex = reinterpret_cast<u64*>(base + L.o_ex);
+    if (var.warp_tiles == 2) {
+        // one cooperative launch: every block resident, phases split by grid barriers
+        const int nw = var.threads / 32;
+        uint64_t dg = (L.n_tiles + nw - 1) / nw;
+        if (dg > (uint64_t)grid) dg = (uint64_t)grid;
+        void* fargs[] = {(void*)&p, (void*)&xp, (void*)&agg, (void*)&ex};
+        return cudaLaunchCooperativeKernel(var.kernel, dim3((unsigned)dg), dim3(var.threads), fargs, var.smem_bytes,
+                                           stream);
+    }
+
     // warp tiles: index pass + reduce in one launch, tile scan, decode.  The
     // first launch waits for everything before it (the previous call's decode
     // still reads this workspace); the next two may start early and wait in
     // the kernel for their predecessor.
-    Extent* xp = reinterpret_cast<Extent*>(base + L.o_extent);
-    u64* agg = reinterpret_cast<u64*>(base + L.o_agg);
-    u64* ex = reinterpret_cast<u64*>(base + L.o_ex);
     const uint64_t n_wt_max = L.n_tiles;   // upper bound; the kernels read the true count from *xp
     uint64_t rg = (n_wt_max + 7) / 8;
     const uint64_t rg_cap = (uint64_t)sms * 8;

@@ -303,6 +303,42 @@ __device__ void lookback(const u64* status, long long tile, u32 epoch, WsHeader*
 }
 
 // ---------------------------------------------------------------------------
+// Grid barrier of a cooperative launch (every block resident): the last
+// block to arrive resets the count and advances the generation the others
+// wait on.  The wait is bounded like the look-back's: on giving up the
+// status word gets ERRB_TIMEOUT, the abort flag is set (later barriers of the
+// launch then pass at once) and the block carries on; its later writes stay
+// in bounds.  Every thread of the block calls it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void grid_barrier(WsHeader* ws) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile u32* gen = &ws->bar_gen;
+        const u32 g = *gen;
+        __threadfence();
+        if (atomicAdd(&ws->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&ws->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ws->bar_gen, 1u);
+        } else {
+            const u32 lim = *(volatile u32*)&ws->spin_limit;
+            const u32 limit = lim ? lim : kSpinLimit;
+            u32 spins = 0;
+            while (*gen == g) {
+                if (++spins > limit || *(volatile u32*)&ws->abort != 0u) {
+                    atomicOr(&ws->status, ERRB_TIMEOUT);
+                    *(volatile u32*)&ws->abort = 1u;
+                    break;
+                }
+                if (spins > 8) __nanosleep(spins < 64 ? 64u : 500u);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // A token of up to 16 bytes (zero padded, words t.x..t.w) moved to byte
 // position f < 16 of a 32-byte span: s[0..7] = the span's words.
 // ---------------------------------------------------------------------------
@@ -700,6 +736,7 @@ __device__ __forceinline__ void finish_launch(WsHeader* ws, u32 epoch) {
             ws->exit_counter = 0;
             ws->abort = 0;
             ws->spin_limit = 0;
+            ws->bar_count = 0;
             u32 ne = (epoch + 1u) & kEpochMask;
             if (ne == 0u) ne = 1u;
             ws->epoch = ne;

@@ -33,7 +33,9 @@ struct WsHeader {
     unsigned int abort;          // set when a bounded wait gave up
     unsigned int queue_counter[3];   // batched decode: next tile ticket of each codec queue
     unsigned int spin_limit;     // polls before a look-back gives up (0 = the built-in limit); reset per launch
-    unsigned int pad[19];
+    unsigned int bar_count;      // one-launch decode: blocks arrived at the current grid barrier
+    unsigned int bar_gen;        // one-launch decode: grid barriers passed
+    unsigned int pad[17];
 };
 constexpr size_t kWsHeaderBytes = 128;
 static_assert(sizeof(WsHeader) == kWsHeaderBytes, "workspace header size");
@@ -131,7 +133,8 @@ struct Variant {
     size_t smem_bytes;
     const void* kernel;   // the decode kernel
     int warp_tiles;       // 0: block pipeline (one launch after the index pass);
-                          // 1: warp tiles (index pass + reduce, tile scan and warp decode launches)
+                          // 1: warp tiles (index pass + reduce, tile scan and warp decode launches);
+                          // 2: warp tiles in one cooperative launch (small columns)
     int width;            // dictionary read width W: 16 = whole entry, 8 = split read (low plane,
                           // high plane only for tokens longer than 8 bytes; paper Sec. 3.2)
     const void* reduce;   // warp tiles: the reduce kernel (its first blocks run the index pass)

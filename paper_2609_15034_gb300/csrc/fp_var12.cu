@@ -15,6 +15,8 @@ const Variant* variants_onpair12(int* n) {
         make_warp_variant<FP_ONPAIR12, 16, false, 20, 1, 16>(),
         make_warp_variant<FP_ONPAIR12, 16, true, 16, 1, 16>(),    // both planes from shared memory
         make_warp_variant<FP_ONPAIR12, 16, false, 20, 1, 8>(),    // split read from the global planes
+        make_fused_variant<FP_ONPAIR12, 16, false, 16, 16>(),   // one launch (small columns)
+        make_fused_variant<FP_ONPAIR12, 16, true, 16, 16>(),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

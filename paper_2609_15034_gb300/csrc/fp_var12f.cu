@@ -9,6 +9,7 @@ const Variant* variants_fsst12(int* n) {
         make_warp_variant<FP_FSST12, 16, true, 16, 1, 8>(),
         make_warp_variant<FP_FSST12, 16, false, 20, 1, 8>(),
         make_warp_variant<FP_FSST12, 32, true, 16, 1, 8>(),
+        make_fused_variant<FP_FSST12, 16, true, 16, 8>(),   // one launch (small columns)
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

@@ -11,6 +11,7 @@ const Variant* variants_onpair16(int* n) {
         make_warp_variant<FP_ONPAIR16, 16, false, 8, 2, 16>(),
         make_warp_variant<FP_ONPAIR16, 16, false, 16, 1, 16>(),
         make_warp_variant<FP_ONPAIR16, 16, false, 16, 1, 8>(),   // split read from the global planes
+        make_fused_variant<FP_ONPAIR16, 16, false, 16, 16>(),   // one launch (small columns)
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;

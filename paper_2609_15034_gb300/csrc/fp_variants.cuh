@@ -44,6 +44,21 @@ Variant make_warp_variant() {
     return v;
 }
 
+// Warp tiles in one cooperative launch (small columns).
+template <int CODEC, int K, bool DSMEM, int NW, int W>
+Variant make_fused_variant() {
+    typedef WarpCore<CODEC, K, DSMEM, W> C;
+    Variant v{};
+    v.threads = NW * 32;
+    v.slots_per_thread = K;
+    v.dict_smem = DSMEM ? 1 : 0;
+    v.smem_bytes = (size_t)C::DICT_BYTES + (DSMEM ? (size_t)C::LENS_BYTES : 0) + NW * sizeof(WarpArea<K>);
+    v.kernel = (const void*)&fused_decode_kernel<CODEC, K, DSMEM, NW, W>;
+    v.warp_tiles = 2;
+    v.width = W;
+    return v;
+}
+
 // Packed codes (run-time width): the warp-tile decoder with a per-lane
 // shared-memory scratch for the code words.
 template <int CODEC, bool DSMEM, int NW>

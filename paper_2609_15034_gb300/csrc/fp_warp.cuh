@@ -502,12 +502,18 @@ struct WarpCore {
         u32 pos[PB];
     };
 
+    // Loads of data written by this launch's earlier phases (the one-launch
+    // decode, CG) bypass L1; otherwise the read-only path.
+    template <bool CG, class T>
+    static __device__ __forceinline__ T ld(const T* a) { return CG ? __ldcg(a) : __ldg(a); }
+
     // Issue the loads of tile t whose boundaries [lo, hi) are already known.
+    template <bool CG = false>
     static __device__ __forceinline__ void fetch(const DecodeParams& p, const Extent& x, const u64* ex, u64 t, u32 lo,
                                                  u32 hi, Fetch& f) {
         const u32 lane = threadIdx.x & 31u;
         f.fast = load_fast(p, lane_q0(x, t), f.wv);
-        f.ex = __ldg(ex + t);
+        f.ex = ld<CG>(ex + t);
         f.lo = lo;
         f.hi = hi;
 #pragma unroll
@@ -518,10 +524,11 @@ struct WarpCore {
     }
 
     // Boundaries [lo, hi) of tile t, clamped to the column's.
+    template <bool CG = false>
     static __device__ __forceinline__ void bounds(const DecodeParams& p, u64 t, u32& lo, u32& hi) {
         const u64 nb = (u64)p.n_strings + 1;
-        lo = __ldg(p.first + t);
-        hi = __ldg(p.first + t + 1);
+        lo = ld<CG>(p.first + t);
+        hi = ld<CG>(p.first + t + 1);
         if ((u64)lo > nb) lo = (u32)nb;
         if ((u64)hi > nb) hi = (u32)nb;
         if (hi < lo) hi = lo;
@@ -534,6 +541,7 @@ struct WarpCore {
     // byte total, recomputed here, must bring it to ex_tiles[t + 1], else
     // ERRB_MISMATCH is raised (a self-check of the two passes, one load
     // per tile).
+    template <bool CG = false>
     static __device__ __forceinline__ void decode_tile(const DecodeParams& p, const Extent& x, u64 t, const Fetch& f,
                                                        const u64* ex_tiles, const uint4* dict, const uint8_t* lens,
                                                        WarpArea<K>& area, u32& err, u32* pk = nullptr) {
@@ -543,7 +551,7 @@ struct WarpCore {
         const u64 ex = f.ex;
         // low word of the next tile's offset (lane 0 checks), in flight during the tile
         const bool chk = lane == 0u && t + 1 < x.n_tiles;
-        const u32 ex_next = chk ? __ldg(reinterpret_cast<const u32*>(ex_tiles + t + 1)) : 0u;
+        const u32 ex_next = chk ? ld<CG>(reinterpret_cast<const u32*>(ex_tiles + t + 1)) : 0u;
         R r;
         finish_load(p, x, q0, f.wv, f.fast, lens, r, pk);
         r.t = (u32)t;
@@ -702,6 +710,32 @@ struct WarpCore {
         }
         if (chk && ex_next != (u32)tile_incl) err |= ERRB_MISMATCH;
         __syncwarp();   // the area is reused by the next tile
+    }
+
+    // Decode the tiles t0, t0 + step, ... of the column (every lane of the
+    // warp).  Software pipeline: while tile t decodes, the inputs of
+    // t + step are in flight and the boundaries of t + 2 step are being read.
+    template <bool CG = false>
+    static __device__ __forceinline__ void decode_tiles(const DecodeParams& p, const Extent& x, const u64* ex, u64 t,
+                                                        u64 step, const uint4* dict, const uint8_t* lens,
+                                                        WarpArea<K>& area, u32& err, u32* pk) {
+        if (t >= x.n_tiles) return;
+        Fetch cur;
+        u32 lo, hi, lo1 = 0, hi1 = 0;
+        bounds<CG>(p, t, lo, hi);
+        fetch<CG>(p, x, ex, t, lo, hi, cur);
+        if (t + step < x.n_tiles) bounds<CG>(p, t + step, lo1, hi1);
+        for (; t < x.n_tiles; t += step) {
+            Fetch nxt;
+            const u64 tn = t + step, t2 = t + 2 * step;
+            u32 lo2 = 0, hi2 = 0;
+            if (tn < x.n_tiles) fetch<CG>(p, x, ex, tn, lo1, hi1, nxt);
+            if (t2 < x.n_tiles) bounds<CG>(p, t2, lo2, hi2);
+            decode_tile<CG>(p, x, t, cur, ex, dict, lens, area, err, pk);
+            cur = nxt;
+            lo1 = lo2;
+            hi1 = hi2;
+        }
     }
 };
 
@@ -919,33 +953,111 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
     grid_wait();   // the tile scan's offsets (the dictionary staging above overlapped it)
     const Extent x = *xp;
     const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
-    WarpArea<K>& area = areas[threadIdx.x >> 5];
-    const u64 warps = (u64)gridDim.x * NW;
     u32 err = 0;
-    u64 t = (u64)blockIdx.x * NW + (threadIdx.x >> 5);
-    if (t < x.n_tiles) {
-        // Software pipeline: while tile t decodes, the inputs of t + warps are
-        // in flight and the boundaries of t + 2 * warps are being read.
-        typename C::Fetch cur;
-        u32 lo, hi, lo1 = 0, hi1 = 0;
-        C::bounds(p, t, lo, hi);
-        C::fetch(p, x, ex, t, lo, hi, cur);
-        if (t + warps < x.n_tiles) C::bounds(p, t + warps, lo1, hi1);
-        for (; t < x.n_tiles; t += warps) {
-            typename C::Fetch nxt;
-            const u64 tn = t + warps, t2 = t + 2 * warps;
-            u32 lo2 = 0, hi2 = 0;
-            if (tn < x.n_tiles) C::fetch(p, x, ex, tn, lo1, hi1, nxt);
-            if (t2 < x.n_tiles) C::bounds(p, t2, lo2, hi2);
-            C::decode_tile(p, x, t, cur, ex, s_dict, lens, area, err, pk);
-            cur = nxt;
-            lo1 = lo2;
-            hi1 = hi2;
-        }
-    }
+    C::decode_tiles(p, x, ex, (u64)blockIdx.x * NW + (threadIdx.x >> 5), (u64)gridDim.x * NW, s_dict, lens,
+                    areas[threadIdx.x >> 5], err, pk);
     if (err) atomicOr(p.err_word, err);
 }
 
+
+// ---------------------------------------------------------------------------
+// Small columns in one cooperative launch: the three passes above as phases
+// of one kernel, separated by grid barriers (bounded waits), so a column of
+// a few thousand warp tiles pays one launch instead of three.
+//   phase 1  index pass (every thread) and tile elements (every warp);
+//   phase 2  block 0 scans the tile elements (one block is enough for the
+//            sizes this path takes) and checks the decoded size;
+//   phase 3  every warp decodes tiles, as warp_decode_kernel.
+// Data written by earlier phases is read through L2 (ld.global.cg).
+// ---------------------------------------------------------------------------
+// Exclusive scan of n tile elements by one block of NT threads: ex[t] =
+// bytes before tile t | entering state << 63; the decoded size and its
+// checks as the tile scan's last block.
+template <bool FSST, int NT>
+__device__ __forceinline__ void block_scan_tiles(const DecodeParams& p, const u64* agg, u64* ex, u64 n, Elem* s_w) {
+    const u32 lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const u64 per = (n + NT - 1) / NT;
+    const u64 i0 = (u64)threadIdx.x * per, i1 = i0 + per < n ? i0 + per : n;
+    Elem e = elem_identity();
+    for (u64 i = i0; i < i1; ++i) e = then<FSST>(e, wt_unpack<FSST>(__ldcg(agg + i)));
+    Elem inc = e;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        Elem y = shfl_up_e<FSST>(inc, d);
+        if (lane < (u32)d) y = elem_identity();
+        inc = then<FSST>(y, inc);
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    Elem before = elem_identity(), tot = elem_identity();
+    for (int w = 0; w < NT / 32; ++w) {
+        if ((u32)w < warp) before = then<FSST>(before, s_w[w]);
+        tot = then<FSST>(tot, s_w[w]);
+    }
+    Elem lex = shfl_up_e<FSST>(inc, 1);
+    if (lane == 0) lex = elem_identity();
+    lex = then<FSST>(before, lex);
+    u64 ob = lex.b0;   // the column is entered on a code: state 0
+    u32 os = FSST ? (lex.n & 1u) : 0u;
+    for (u64 i = i0; i < i1; ++i) {
+        ex[i] = ob | ((u64)os << 63);
+        const Elem ek = wt_unpack<FSST>(__ldcg(agg + i));
+        ob += (FSST && os) ? ek.b1 : ek.b0;
+        os = FSST ? ((ek.n >> os) & 1u) : 0u;
+    }
+    if (threadIdx.x == 0) {
+        const u64 total = tot.b0;
+        *p.total_out = total;
+        if (total > p.capacity && !p.size_only) atomicOr(p.err_word, ERRB_CAPACITY);
+        if (total > 0x7fffffffull) atomicOr(p.err_word, ERRB_OVERFLOW);
+    }
+}
+
+template <int CODEC, int K, bool DSMEM, int NW, int W = WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16>
+__global__ void __launch_bounds__(NW * 32, 1) fused_decode_kernel(const DecodeParams p, Extent* xp, u64* agg,
+                                                                   u64* ex) {
+    typedef WarpCore<CODEC, K, DSMEM, W> C;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Elem s_w[NW];
+    uint4* s_dict = reinterpret_cast<uint4*>(smem_raw);
+    uint8_t* s_lens = smem_raw + C::DICT_BYTES;
+    WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
+    if (DSMEM) {
+        const uint4* src = reinterpret_cast<const uint4*>(C::TOK8 ? p.dict.table : p.dict.planes);
+        for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
+        const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
+        for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
+        __syncthreads();
+    }
+    const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
+    const u32 epoch = *(volatile u32*)&p.ws->epoch;
+    const Extent x = column_extent(p, C::TILE);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
+    const u32 lane = threadIdx.x & 31u;
+    const u64 gwarp = (u64)blockIdx.x * NW + (threadIdx.x >> 5), gwarps = (u64)gridDim.x * NW;
+    u32 err = 0;
+    // phase 1
+    index_groups(p, x, (u32)(__ffs(C::TILE) - 1), 0, (u64)p.n_strings + 1, (u64)blockIdx.x * blockDim.x + threadIdx.x,
+                 (u64)gridDim.x * blockDim.x, const_cast<u32*>(p.first));
+    for (u64 t = gwarp; t < x.n_tiles; t += gwarps) {
+        u32 wv[C::LANE_WORDS];
+        const u64 q0 = C::lane_q0(x, t);
+        const bool fast = C::load_fast(p, q0, wv);
+        typename C::R r;
+        C::finish_load(p, x, q0, wv, fast, lens, r);
+        const TElem e = C::tile_element(r, lane, err);
+        if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
+    }
+    grid_barrier(p.ws);
+    // phase 2
+    if (blockIdx.x == 0) block_scan_tiles<C::FSST, NW * 32>(p, agg, ex, x.n_tiles, s_w);
+    grid_barrier(p.ws);
+    // phase 3
+    C::template decode_tiles<true>(p, x, ex, gwarp, gwarps, s_dict, lens, areas[threadIdx.x >> 5], err, nullptr);
+    if (err) atomicOr(p.err_word, err);
+    __syncthreads();
+    finish_launch(p.ws, epoch);   // the last block out clears the abort flag and the stall settings
+}
 
 }  // namespace
 }  // namespace fp

@@ -61,14 +61,15 @@ def test_variant_tables_and_size_defaults():
     itself consistently, the default for any code-buffer size is a valid
     variant, a selection overrides it for every size and -1 restores it."""
     import paper_2609_15034_gb300 as fp
-    for codec in (fp.ONPAIR16, fp.ONPAIR12, fp.FSST8):
+    for codec in (fp.ONPAIR16, fp.ONPAIR12, fp.FSST8, fp.FSST12):
         n = fp.variant_count(codec)
         assert n >= 2
         for v in range(n):
             info = fp.variant_info(codec, v)
             assert info["threads"] % 32 == 0 and 32 <= info["threads"] <= 1024
             assert info["slots_per_thread"] in (8, 16, 32)
-            assert info["launches_per_call"] in (2, 3)
+            assert info["launches_per_call"] in (1, 2, 3)   # one cooperative launch, block pipeline, warp tiles
+            assert fp.variant_width(codec, v) in ((8, 16) if codec in (fp.ONPAIR16, fp.ONPAIR12) else (8,))
             if codec == fp.ONPAIR16:
                 assert not info["dict_in_smem"]   # a 1 MiB table does not fit
         sizes = [0, 1, 16, 1 << 20, (1 << 22) - 1, 1 << 22, 1 << 24, 1 << 26, 1 << 30, 1 << 34]

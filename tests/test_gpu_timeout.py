@@ -8,7 +8,8 @@ decode on the same stream must be normal and equal the oracle's.
 
 Columns span several tickets: more than 2,048 warp tiles (two tile-scan
 blocks) for the warp-tile decoder, and several 4,096-slot tiles for the
-block pipeline."""
+block pipeline.  The one-launch decode's first grid barrier is made to
+wait for an arrival count no grid reaches."""
 import numpy as np
 import pytest
 
@@ -25,29 +26,28 @@ def fp():
         pytest.skip("no CUDA device")
     import paper_2609_15034_gb300 as m
     yield m
-    for c in (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8):
+    for c in (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8, synth.FSST12):
         m.variant_select(c, -1)
 
 
-def block_pipeline_variant(fp, codec):
+def variant_with_launches(fp, codec, launches):
     for v in range(fp.variant_count(codec)):
-        if fp.variant_info(codec, v)["launches_per_call"] == 2:
+        if fp.variant_info(codec, v)["launches_per_call"] == launches:
             return v
-    raise AssertionError("no block-pipeline variant")
+    raise AssertionError(f"no variant with {launches} launches per call")
 
 
-@pytest.mark.parametrize("codec,n,block_pipeline", [
-    (synth.ONPAIR16, 60_000, False),    # ~1.2M slots: 2,300 warp tiles of 512
-    (synth.FSST8, 200_000, False),      # ~2.4M slots: 2,400 warp tiles of 1,024
-    (synth.ONPAIR12, 30_000, True),     # ~0.5M slots: 130 block tiles of 4,096
+@pytest.mark.parametrize("codec,n,launches", [
+    (synth.ONPAIR16, 60_000, 3),    # warp tiles: ~1.2M slots, 2,300 warp tiles of 512
+    (synth.FSST8, 200_000, 3),      # ~2.4M slots: 2,400 warp tiles of 1,024
+    (synth.ONPAIR12, 30_000, 2),    # block pipeline: ~0.5M slots, 130 block tiles of 4,096
+    (synth.ONPAIR16, 20_000, 1),    # one cooperative launch: its first grid barrier
+    (synth.FSST12, 20_000, 1),
 ])
-def test_lookback_gives_up_then_recovers(fp, codec, n, block_pipeline):
+def test_lookback_gives_up_then_recovers(fp, codec, n, launches):
     import torch
     col = synth.column(codec, 900 + codec, n)
-    if block_pipeline:
-        fp.variant_select(codec, block_pipeline_variant(fp, codec))
-    else:
-        fp.variant_select(codec, -1)
+    fp.variant_select(codec, variant_with_launches(fp, codec, launches))
     try:
         dc = DeviceColumn(col)
         ref = oracle_decode(col)
