@@ -167,9 +167,11 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def workload_column(name: str, seed: int):
-    """The workload's column and, for cascaded workloads, its bits per stored code."""
-    codec, n, _ = WORKLOADS[name]
+def workload_column(name: str, seed: int, n: int = 0):
+    """The workload's column (n strings; 0: the workload's own count) and, for
+    cascaded workloads, its bits per stored code."""
+    codec, n_default, _ = WORKLOADS[name]
+    n = n or n_default
     if name in PACKED_WORKLOADS:
         bits, n_entries = PACKED_WORKLOADS[name]
         col = synth.fsst12_column(seed, n, dictionary=synth.fsst12_dictionary(seed, n_entries))
@@ -212,7 +214,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     codec, n, desc = WORKLOADS[args.workload]
-    col, packed_bits = workload_column(args.workload, 0)
+    if args.n_strings:
+        n = args.n_strings
+    col, packed_bits = workload_column(args.workload, 0, n)
     threads = 1 if packed_bits else (os.cpu_count() or 1)
     vals, samples = [], []
     per_step = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
@@ -249,7 +253,8 @@ def run_ours(args, rank, world, local_rank):
     codec, n, desc = WORKLOADS[args.workload]
     if args.n_strings:
         n = args.n_strings
-    col, packed_bits = workload_column(args.workload, rank)   # one independent replica column per rank
+    col, packed_bits = workload_column(args.workload, rank, n)   # one independent replica column per rank
+    assert col.n_strings == n
     fp.variant_select(codec, args.variant)
 
     stream = torch.cuda.current_stream()

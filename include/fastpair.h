@@ -529,9 +529,10 @@ fp_status fp_serve_destroy(fp_server* server);
  *                   passes as phases of one cooperative launch, for small
  *                   columns).  Any out pointer may be NULL.
  * fp_variant_select make variant v the one fp_decode uses for the codec in
- *                   this process (v = -1 restores the built-in defaults,
- *                   which depend on the size of the code buffer and on the
- *                   dictionary's read width).
+ *                   this process (v = -1 restores the defaults: tuned ones
+ *                   (fp_tune_*), else built-in ones, which depend on the
+ *                   size of the code buffer and on the dictionary's read
+ *                   width).
  * fp_variant_selected  the variant selected for the codec, or with none
  *                   selected the default for large code buffers.
  * fp_variant_for    the variant fp_decode uses for a code buffer of
@@ -543,6 +544,30 @@ fp_status fp_variant_info(fp_codec codec, int v, uint32_t* threads, uint32_t* sl
 fp_status fp_variant_select(fp_codec codec, int v);
 int fp_variant_selected(fp_codec codec);
 int fp_variant_for(fp_codec codec, uint64_t codes_bytes);
+
+/*
+ * Autotuning of the single-column decode (no counterpart API in the paper,
+ * whose shapes are chosen per column by hand, Sec. 4.1-4.4).
+ *
+ * fp_tune_column -- time every compiled variant of the codec whose read
+ *   width equals the dictionary's (one warm-up, best of three decodes of
+ *   the caller's column; inputs and outputs as fp_decode, which the runs
+ *   write) and make the fastest the default for this device, codec, width
+ *   and size class (floor(log2) of the code buffer's slots).  table_path:
+ *   NULL, or a text file the choice is appended to ("sms codec width class
+ *   variant ms").  *chosen / *best_ms (may be NULL) receive the variant and
+ *   its time.  Synchronous.  Returns the column's data status.
+ * fp_tune_load -- read such a file: its lines for this library's variants
+ *   become defaults (entries for another SM count stay unused).
+ * fp_tune_clear -- forget the tuned defaults (the built-in ones apply).
+ * A variant selected with fp_variant_select overrides tuned defaults.
+ */
+fp_status fp_tune_column(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                         const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                         uint64_t out_capacity, uint32_t* d_out_offsets, const char* table_path, fp_stream_t stream,
+                         int* chosen, float* best_ms);
+fp_status fp_tune_load(const char* table_path);
+fp_status fp_tune_clear(void);
 
 /* The variant fp_decode uses with this dictionary (its codec and read
  * width) for a code buffer of codes_bytes bytes; -1 for NULL.  fp_variant_for

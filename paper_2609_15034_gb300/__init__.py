@@ -63,6 +63,9 @@ def lib() -> ctypes.CDLL:
             L.fp_rows_size.argtypes = [I, P, P, U64, P, U32, P, U32, P, ctypes.POINTER(U64), ctypes.POINTER(U64)]
             L.fp_decode_rows.argtypes = [I, P, P, U64, P, U32, P, U32, U64, P, U64, P, P]
             L.fp_decode_packed.argtypes = [I, P, U32, P, U64, P, U32, P, U64, P, P]
+            L.fp_tune_column.argtypes = [I, P, P, U64, P, U32, P, U64, P, ctypes.c_char_p, P,
+                                         ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
+            L.fp_tune_load.argtypes = [ctypes.c_char_p]
             L.fp_decoded_size_packed.argtypes = [I, P, U32, P, U64, P, U32, P, ctypes.POINTER(U64)]
             L.fp_last_error.restype = ctypes.c_char_p
             L.fp_variant_count.argtypes = [I]
@@ -102,13 +105,19 @@ def lib() -> ctypes.CDLL:
                          "fp_decode_noalloc",
                          "fp_sync_status", "fp_debug_stall_next", "fp_variant_info", "fp_variant_select",
                          "fp_dict_set_width", "fp_rows_size", "fp_decode_rows", "fp_decode_packed",
-                         "fp_decoded_size_packed",
+                         "fp_decoded_size_packed", "fp_tune_column", "fp_tune_load", "fp_tune_clear",
                          "fp_plan_create", "fp_plan_create_config", "fp_decode_batch", "fp_plan_sync_status",
                          "fp_plan_info", "fp_plan_destroy", "fp_batch_config_info", "fp_serve_create",
                          "fp_serve_dict_put", "fp_serve_submit", "fp_serve_poll", "fp_serve_release",
                          "fp_serve_stats", "fp_serve_destroy", "fp_sidecar_build", "fp_decode_sidecar"):
                 getattr(L, name).restype = I
             _lib = L
+            # the committed tuning table of this library's shapes (defaults per
+            # GPU model and column size; unused on another SM count)
+            import os
+            table = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.txt")
+            if os.path.exists(table):
+                L.fp_tune_load(table.encode())
     return _lib
 
 
@@ -403,6 +412,24 @@ def variant_for_dict(d: Dict, codes_bytes: int) -> int:
     """The variant fp_decode uses with dictionary ``d`` for a code buffer of
     codes_bytes bytes."""
     return lib().fp_variant_for_dict(d.handle, codes_bytes)
+
+
+def tune_column(codec, d: Dict, codes_ptr: int, codes_bytes: int, code_offsets_ptr: int, n_strings: int,
+                out_ptr: int, capacity: int, out_offsets_ptr: int, table_path: str | None = None, stream=None):
+    """fp_tune_column: (status, chosen variant, its ms)."""
+    v, ms = ctypes.c_int(-1), ctypes.c_float(0.0)
+    st = lib().fp_tune_column(codec, d.handle, codes_ptr, codes_bytes, code_offsets_ptr, n_strings, out_ptr, capacity,
+                              out_offsets_ptr, table_path.encode() if table_path else None, _stream(stream),
+                              ctypes.byref(v), ctypes.byref(ms))
+    return st, v.value, ms.value
+
+
+def tune_load(table_path: str) -> int:
+    return _check(lib().fp_tune_load(table_path.encode()), "fp_tune_load")
+
+
+def tune_clear() -> int:
+    return lib().fp_tune_clear()
 
 
 def variant_width(codec: int, v: int) -> int:

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -111,11 +112,38 @@ Workspace* find_workspace(cudaStream_t stream) {
 // ---- variants and occupancy ----------------------------------------------------
 std::atomic<int> g_selected[5] = {{-1}, {-1}, {-1}, {-1}, {-1}};
 
-// The selected variant, else the default for a code buffer of max_slots and
-// a dictionary read width.
+// Tuned shapes: (SM count, codec, read width, size class = floor(log2 of the
+// code slots)) -> variant, from fp_tune_column or a loaded tuning file.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned;
+std::atomic<int> g_tuned_any{0};
+int g_sms_cached = 0;   // SM count of the device the first tuned lookup ran on
+
+int size_class(uint64_t max_slots) {
+    int c = 0;
+    while (c < 63 && (max_slots >> (c + 1)) != 0) ++c;
+    return c;
+}
+
+int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+// The selected variant, else a tuned one for this device, codec, width and
+// size class, else the built-in default.
 int selected_variant(int codec, uint64_t max_slots, int width) {
     const int v = g_selected[codec].load();
-    return v >= 0 ? v : variant_default(codec, max_slots, width);
+    if (v >= 0) return v;
+    if (g_tuned_any.load()) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (!g_sms_cached) g_sms_cached = device_sms();
+        auto it = g_tuned.find(std::make_tuple(g_sms_cached, codec, width, size_class(max_slots)));
+        if (it != g_tuned.end() && variant_get(codec, it->second)) return it->second;
+    }
+    return variant_default(codec, max_slots, width);
 }
 
 struct DevInfo {
@@ -215,10 +243,11 @@ fp_status take_status(Workspace* w, uint64_t* total, cudaStream_t stream) {
 fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
                      const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
                      uint64_t out_capacity, uint32_t* d_out_offsets, cudaStream_t stream, bool size_only,
-                     Workspace** ws_out, uint32_t packed_bits = 0) {
+                     Workspace** ws_out, uint32_t packed_bits = 0, int force_variant = -1) {
     const uint64_t max_slots = packed_bits ? codes_bytes * 8 / packed_bits : max_slots_of(codec, codes_bytes);
-    const Variant* var = packed_bits ? variant_packed(codec)
-                                     : variant_get(codec, selected_variant(codec, max_slots, dict->width));
+    const Variant* var = packed_bits          ? variant_packed(codec)
+                         : force_variant >= 0 ? variant_get(codec, force_variant)
+                                              : variant_get(codec, selected_variant(codec, max_slots, dict->width));
     if (!var) return fail(FP_ERR_ARG, "no decode variant for codec %d", (int)codec);
     if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
     const uint64_t tile = variant_tile(*var);
@@ -235,7 +264,7 @@ fp_status run_decode(fp_codec codec, const fp_dict* dict, const void* d_codes, u
                                         stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     }
-    DecodeParams p;
+    DecodeParams p{};
     p.dict = dict->view();
     p.codes = static_cast<const uint8_t*>(d_codes);
     p.codes_bytes = codes_bytes;
@@ -301,7 +330,7 @@ fp_status run_rows(fp_codec codec, const fp_dict* dict, const void* d_codes, uin
                      n_strings, d_row_ids, n_rows};
     cudaError_t e = launch_rows_gather(codec, a, slots, true, rows, RL, ws, sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "row gather launch");
-    DecodeParams p;
+    DecodeParams p{};
     p.dict = dict->view();
     p.codes = reinterpret_cast<const uint8_t*>(rows + RL.o_codes);
     p.codes_bytes = RL.codes_bytes;
@@ -514,6 +543,93 @@ fp_status fp_decoded_size_packed(fp_codec codec, const fp_dict* dict, uint32_t c
     return take_status(w, h_total, stream);
 }
 
+fp_status fp_tune_column(fp_codec codec, const fp_dict* dict, const void* d_codes, uint64_t codes_bytes,
+                         const uint32_t* d_code_offsets, uint32_t n_strings, uint8_t* d_out_bytes,
+                         uint64_t out_capacity, uint32_t* d_out_offsets, const char* table_path, fp_stream_t stream_,
+                         int* chosen, float* best_ms) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    fp_status st = check_common(codec, dict, d_codes, codes_bytes, d_code_offsets, d_out_bytes, out_capacity,
+                                d_out_offsets, true);
+    if (st != FP_OK) return st;
+    if (n_strings == 0xffffffffu) return fail(FP_ERR_ARG, "n_strings must be below 2^32-1");
+    const uint64_t max_slots = max_slots_of(codec, codes_bytes);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    int best = -1;
+    float best_t = 0.0f;
+    const int nv = variant_count(codec);
+    for (int v = 0; v < nv && st == FP_OK; ++v) {
+        if (variant_get(codec, v)->width != dict->width) continue;   // the dictionary's read width only
+        float t_best = -1.0f;
+        for (int r = 0; r < 4 && st == FP_OK; ++r) {   // one warm-up, best of three
+            e = cudaEventRecord(a, stream);
+            if (e == cudaSuccess)
+                st = run_decode(codec, dict, d_codes, codes_bytes, d_code_offsets, n_strings, d_out_bytes,
+                                out_capacity, d_out_offsets, stream, false, nullptr, 0, v);
+            if (e == cudaSuccess && st == FP_OK) e = cudaEventRecord(b, stream);
+            if (e == cudaSuccess && st == FP_OK) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess && st == FP_OK) e = cudaEventElapsedTime(&ms, a, b);
+            if (e != cudaSuccess && st == FP_OK) st = cuda_fail(e, "tuning run");
+            if (st == FP_OK && r > 0 && (t_best < 0.0f || ms < t_best)) t_best = ms;
+        }
+        if (st == FP_OK && (best < 0 || t_best < best_t)) {
+            best = v;
+            best_t = t_best;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != FP_OK) return st;
+    // a data error in the column makes its timings meaningless
+    st = fp_sync_status(stream_);
+    if (st != FP_OK) return st;
+    const int sms = device_sms();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[std::make_tuple(sms, (int)codec, dict->width, size_class(max_slots))] = best;
+        g_tuned_any.store(1);
+    }
+    if (table_path) {
+        FILE* f = fopen(table_path, "a");
+        if (!f) return fail(FP_ERR_ARG, "cannot open tuning table %s", table_path);
+        fprintf(f, "%d %d %d %d %d %.4f\n", sms, (int)codec, dict->width, size_class(max_slots), best, best_t);
+        fclose(f);
+    }
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
+    return FP_OK;
+}
+
+fp_status fp_tune_load(const char* table_path) {
+    if (!table_path) return fail(FP_ERR_ARG, "table_path is NULL");
+    FILE* f = fopen(table_path, "r");
+    if (!f) return fail(FP_ERR_ARG, "cannot open tuning table %s", table_path);
+    int sms, codec, width, cls, v, n = 0;
+    float ms;
+    char line[256];
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        if (sscanf(line, "%d %d %d %d %d %f", &sms, &codec, &width, &cls, &v, &ms) != 6) continue;
+        if (!valid_codec(codec) || !variant_get(codec, v)) continue;   // built for another library
+        g_tuned[std::make_tuple(sms, codec, width, cls)] = v;   // later lines win
+        ++n;
+    }
+    fclose(f);
+    if (n) g_tuned_any.store(1);
+    return FP_OK;
+}
+
+fp_status fp_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+    g_tuned_any.store(0);
+    return FP_OK;
+}
+
 int fp_width_for_histogram(const uint64_t* hist17) { return hist17 ? width_for_histogram(hist17) : 8; }
 
 fp_status fp_dict_set_width(fp_dict* dict, int width) {
@@ -563,7 +679,7 @@ fp_status fp_decode_plain(fp_codec codec, const fp_dict* dict, const void* d_cod
     const size_t words = plain_scratch_words(n_strings);
     st = get_workspace(stream, 256, words, &w);
     if (st != FP_OK) return st;
-    DecodeParams p;
+    DecodeParams p{};
     memset(&p, 0, sizeof(p));
     p.dict = dict->view();
     p.codes = static_cast<const uint8_t*>(d_codes);
@@ -758,7 +874,7 @@ extern "C" fp_status fp_decode_noalloc(fp_codec codec, const fp_dict* dict, cons
         e = cudaMemsetAsync(base + kWsHeaderBytes, 0, room, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
     }
-    DecodeParams p;
+    DecodeParams p{};
     p.dict = dict->view();
     p.codes = static_cast<const uint8_t*>(d_codes);
     p.codes_bytes = codes_bytes;
