@@ -131,3 +131,27 @@ def test_split_read_rule_against_the_papers_columns():
     expect16 = {k for k, v in table1_short.items() if v < 40}
     for name, pct in table1_short.items():
         assert (fp.width_for_histogram(hist(pct)) == 16) == (name in expect16), name
+
+
+def test_committed_tuning_table_names_compiled_shapes():
+    """The tuning table the binding loads at start-up: every entry names a
+    codec, a read width that codec has, and a compiled variant of that
+    width; every codec has entries."""
+    import paper_2609_15034_gb300 as fp
+    path = os.path.join(ROOT, "paper_2609_15034_gb300", "tuning", "gb300.txt")
+    if not os.path.exists(path):
+        pytest.skip("no tuning table committed")
+    seen = set()
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            sms, codec, width, cls, v, ms = line.split()
+            sms, codec, width, cls, v = int(sms), int(codec), int(width), int(cls), int(v)
+            assert sms > 0 and 0 <= cls < 64 and float(ms) > 0
+            assert codec in (fp.ONPAIR16, fp.ONPAIR12, fp.FSST8, fp.FSST12)
+            assert 0 <= v < fp.variant_count(codec)
+            assert fp.variant_width(codec, v) == width
+            seen.add(codec)
+    assert seen == {fp.ONPAIR16, fp.ONPAIR12, fp.FSST8, fp.FSST12}
+    assert fp.tune_load(path) == fp.OK
