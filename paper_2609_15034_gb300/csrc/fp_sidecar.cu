@@ -92,9 +92,9 @@ struct Path {
     static size_t decode_smem() {
         return (size_t)C::DICT_BYTES + (DSMEM ? (size_t)C::LENS_BYTES : 0) + kSidecarWarps * sizeof(WarpArea<K>);
     }
-    // dictionary reads: split planes for the staged OnPair-12 table, whole
-    // entries for OnPair-16 through L1, 8-byte entries for the FSST codecs
-    static constexpr int W = CODEC == FP_ONPAIR16 ? 16 : 8;
+    // dictionary reads: whole 16-byte entries for the OnPair codecs (staged
+    // for OnPair-12, through L1 for OnPair-16), 8-byte entries for FSST
+    static constexpr int W = (CODEC == FP_ONPAIR16 || CODEC == FP_ONPAIR12) ? 16 : 8;
     static const void* decode_kernel() {
         return (const void*)&warp_decode_kernel<CODEC, K, DSMEM, kSidecarWarps, 1, W>;
     }

@@ -423,16 +423,18 @@ struct WarpCore {
         return TElem{b0, b1, __shfl_sync(0xffffffffu, e, 31)};
     }
 
-    // Token of `code` (zero padded to 16 bytes).  OnPair: planes staged in
-    // shared memory (DSMEM) or read through L1 from the global planes (W = 8)
-    // or the 16-byte table (W = 16).  FSST-12: 8-byte entries.
+    // Token of `code` (zero padded to 16 bytes), from the table staged in
+    // shared memory (DSMEM) or through L1.  OnPair: the whole 16-byte entry
+    // (W = 16) or the low plane and, for longer tokens, the high plane
+    // (W = 8).  FSST: 8-byte entries.
     static __device__ __forceinline__ uint4 token(const DecodeParams& p, const uint4* dict, u32 code, u32 len) {
         if (TOK8) {
             const uint2 d = DSMEM ? reinterpret_cast<const uint2*>(dict)[code]
                                   : __ldg(reinterpret_cast<const uint2*>(p.dict.table) + code);
             return make_uint4(d.x, d.y, 0u, 0u);
         }
-        if (!DSMEM && W == 16) return __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
+        // W = 16: whole 16-byte entries, one load (staged as the table is laid out)
+        if (W == 16) return DSMEM ? dict[code] : __ldg(reinterpret_cast<const uint4*>(p.dict.table) + code);
         const uint2* lo = DSMEM ? reinterpret_cast<const uint2*>(dict) : reinterpret_cast<const uint2*>(p.dict.planes);
         const uint2 a = DSMEM ? lo[code] : __ldg(lo + code);
         uint2 b = make_uint2(0u, 0u);
@@ -484,6 +486,27 @@ struct WarpCore {
             else tok = make_uint4(a == 0u ? 0u : (is_lit ? bt : d.x), (a == 0u || is_lit) ? 0u : d.y, 0u, 0u);
             as.put(tok, a);
         }
+    }
+
+    // Byte count of an escape-free lane whose K slots all lie inside the
+    // column, straight from its code words (constant bit positions): one
+    // extract, one length load and one add per code; a code without a token
+    // (length 0) raises ERRB_CORRUPT.
+    static __device__ __forceinline__ u32 lane_length_sum(const u32 (&wv)[LANE_WORDS], const uint8_t* lens,
+                                                          u32& err) {
+        static_assert(!FSST && !PACKED, "escape-free codecs in their own layout");
+        constexpr u32 MASK = (1u << WBITS) - 1u;
+        u32 sum = 0, mn = 0xffu;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int bit = k * WBITS, w = bit >> 5, sh = bit & 31;
+            const u32 code = (sh + WBITS <= 32) ? ((wv[w] >> sh) & MASK) : (__funnelshift_r(wv[w], wv[w + 1], sh) & MASK);
+            const u32 L = DSMEM ? (u32)lens[code] : (u32)__ldg(lens + code);
+            sum += L;
+            mn = min(mn, L);
+        }
+        if (mn == 0u) err |= ERRB_CORRUPT;
+        return sum;
     }
 
     static __device__ __forceinline__ u64 lane_q0(const Extent& x, u64 t) {
@@ -762,6 +785,7 @@ __global__ void __launch_bounds__(256, ReduceShape<CODEC, K>::MINB) reduce_kerne
     typedef WarpCore<CODEC, K, DSMEM, WarpCore<CODEC, K, DSMEM>::TOK8 ? 8 : 16, PACKED> C;
     __shared__ __align__(16) uint8_t s_lens[DSMEM ? C::LENS_BYTES : 16];
     __shared__ __align__(16) u32 s_pk[PACKED ? 256 * C::PK_STRIDE : 2];   // packed codes: per-lane scratch
+    grid_release();   // the next launch may be scheduled as these blocks retire (it waits for their results)
     if (blockIdx.x < index_blocks) {
         const Extent x = column_extent(p, C::TILE);
         if (blockIdx.x == 0 && threadIdx.x == 0) *xp = x;
@@ -803,10 +827,23 @@ __global__ void __launch_bounds__(256, ReduceShape<CODEC, K>::MINB) reduce_kerne
         for (int u = 0; u < U; ++u) {
             const u64 t = t0 + u * warps;
             if (t < x.n_tiles) {
-                typename C::R r;
-                C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r, s_pk + threadIdx.x * C::PK_STRIDE);
-                const TElem e = C::tile_element(r, lane, err);
-                if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
+                bool done = false;
+                if constexpr (!C::FSST && !PACKED) {
+                    // a whole tile of an escape-free column (all but the edge tiles)
+                    const u64 tile_start = (x.first_tile + t) * (u64)C::TILE;
+                    if (__all_sync(0xffffffffu, fast[u]) && tile_start >= x.c_begin &&
+                        tile_start + C::TILE <= x.c_end) {
+                        const u32 tot = __reduce_add_sync(0xffffffffu, C::lane_length_sum(wv[u], lens, err));
+                        if (lane == 31) agg[t] = tot;
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    typename C::R r;
+                    C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r, s_pk + threadIdx.x * C::PK_STRIDE);
+                    const TElem e = C::tile_element(r, lane, err);
+                    if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
+                }
             }
         }
 #pragma unroll
@@ -942,9 +979,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
     // packed codes: a scratch of PK_STRIDE words per lane after the warp areas
     u32* pk = PACKED ? reinterpret_cast<u32*>(areas + NW) + threadIdx.x * C::PK_STRIDE : nullptr;
     if (DSMEM) {
-        // FSST: the 8-byte entries as they are; OnPair: the two planes (entry
-        // e's bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e)
-        const uint4* src = reinterpret_cast<const uint4*>(C::TOK8 ? p.dict.table : p.dict.planes);
+        // FSST: the 8-byte entries as they are; OnPair read whole (W = 16): the
+        // 16-byte entries; OnPair split read (W = 8): the two planes (entry e's
+        // bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e)
+        const uint4* src = reinterpret_cast<const uint4*>((C::TOK8 || W == 16) ? p.dict.table : p.dict.planes);
         for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
         const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
         for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
@@ -1023,7 +1061,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fused_decode_kernel(const DecodePa
     uint8_t* s_lens = smem_raw + C::DICT_BYTES;
     WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
     if (DSMEM) {
-        const uint4* src = reinterpret_cast<const uint4*>(C::TOK8 ? p.dict.table : p.dict.planes);
+        const uint4* src = reinterpret_cast<const uint4*>((C::TOK8 || W == 16) ? p.dict.table : p.dict.planes);
         for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
         const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
         for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);

@@ -64,7 +64,7 @@ def test_full_size_every_element(fp, name, codec, n):
     d.free()
 
 
-MID = [(synth.ONPAIR12, 300_000), (synth.FSST8, 400_000), (synth.ONPAIR16, 200_000)]
+MID = [(synth.ONPAIR12, 600_000), (synth.FSST8, 1_000_000), (synth.ONPAIR16, 500_000)]
 
 
 @pytest.mark.parametrize("codec,n", MID)
@@ -73,7 +73,7 @@ def test_every_variant_across_scan_blocks(fp, codec, n):
     ref = oracle_decode(col)
     assert ref.status == oracle.OK
     # tiles of 512 or 1,024 slots: several blocks of 2,048 tiles in the tile scan
-    assert col.n_slots > 3 * 2048 * 512
+    assert col.n_slots > 4 * 2048 * 1024
     dc = DeviceColumn(col)
     try:
         for v in range(fp.variant_count(codec)):
