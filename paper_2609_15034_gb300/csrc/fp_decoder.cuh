@@ -440,6 +440,27 @@ struct Assembler {
         c[3] = fl ? s[7] : full.w;
         f &= 15u;   // below 16 before the insert, below 32 after it
     }
+    // Append a token of at most 8 bytes given already moved up by (f & 3)
+    // bytes (y0..y2, zero elsewhere): only whole-word moves remain, no
+    // funnel shifts.  Same stores and chunk handling as put().
+    __device__ __forceinline__ void put3(u32 y0, u32 y1, u32 y2, u32 len) {
+        const bool q1 = (f & 4u) != 0u;
+        const bool q2 = (f & 8u) != 0u;
+        const u32 v0 = q1 ? 0u : y0, v1 = q1 ? y0 : y1, v2 = q1 ? y1 : y2, v3 = q1 ? y2 : 0u;
+        const u32 s0 = q2 ? 0u : v0, s1 = q2 ? 0u : v1, s2 = q2 ? v0 : v2, s3 = q2 ? v1 : v3, s4 = q2 ? v2 : 0u,
+                  s5 = q2 ? v3 : 0u;
+        f += len;
+        const bool fl = f >= 16u;
+        const uint4 full = make_uint4(c[0] | s0, c[1] | s1, c[2] | s2, c[3] | s3);
+        if (fl) *tgt = full;
+        g += fl ? 1 : 0;
+        tgt = fl ? g : tgt;
+        c[0] = fl ? s4 : full.x;
+        c[1] = fl ? s5 : full.y;
+        c[2] = fl ? 0u : full.z;
+        c[3] = fl ? 0u : full.w;
+        f &= 15u;
+    }
     // Close the thread's range; `nonempty` = it produced at least one byte.
     // Afterwards the head slot holds the thread's lead fragment (FA_VALID).
     __device__ __forceinline__ void finish(bool nonempty) {

@@ -128,7 +128,12 @@ struct WarpCore {
     static constexpr int PK_STRIDE = 2 * LANE_WORDS;
     // entries of the table (a staged table, or the global planes)
     static constexpr int kTable = (CODEC == FP_FSST8) ? 256 : (CODEC == FP_ONPAIR16 ? 65536 : 4096);
-    static constexpr int DICT_BYTES = DSMEM ? kTable * (TOK8 ? 8 : 16) : 0;
+    // FSST-8 with a staged table: every symbol and every literal byte kept
+    // moved up by 0..3 bytes (entry lit * 1024 + r * 256 + b, 16 bytes
+    // each), so an insert at byte position f reads the copy for r = f & 3
+    // and needs only whole-word moves.
+    static constexpr bool PRESHIFT = FSST && DSMEM;
+    static constexpr int DICT_BYTES = DSMEM ? (PRESHIFT ? 2 * 4 * 256 * 16 : kTable * (TOK8 ? 8 : 16)) : 0;
     static constexpr int LENS_BYTES = kTable;
     typedef TileRegs<CODEC, K> R;
     static_assert(K == 8 || K == 16 || K == 32, "slots per lane");
@@ -478,6 +483,13 @@ struct WarpCore {
             const u32 bt = code_at<CODEC, K>(r, k);
             const u32 a = (cw[k >> 2] >> ((k & 3) * 8)) & 0xffu;
             const bool is_lit = (lit >> k) & 1u;
+            if (PRESHIFT) {
+                // the copy of the symbol (or literal) moved up by the insert position's byte offset
+                uint4 y = dict[(((lit >> k) & 1u) << 10) | ((as.f & 3u) << 8) | bt];
+                if (!ALLV && a == 0u) y = make_uint4(0u, 0u, 0u, 0u);
+                as.put3(y.x, y.y, y.z, a);
+                continue;
+            }
             uint2 d;
             if (DSMEM) d = reinterpret_cast<const uint2*>(dict)[bt];
             else d = __ldg(reinterpret_cast<const uint2*>(p.dict.table) + bt);
@@ -486,6 +498,35 @@ struct WarpCore {
             else tok = make_uint4(a == 0u ? 0u : (is_lit ? bt : d.x), (a == 0u || is_lit) ? 0u : d.y, 0u, 0u);
             as.put(tok, a);
         }
+    }
+
+    // Stage the dictionary and the token lengths in shared memory (every
+    // thread of the block; the caller synchronises).  FSST: the 8-byte
+    // entries, or for FSST-8 the moved-up copies (PRESHIFT); OnPair read
+    // whole (W = 16): the 16-byte entries; OnPair split read (W = 8): the two
+    // planes (entry e's bytes 0..7 at low-plane word e, bytes 8..15 at
+    // high-plane word e).
+    static __device__ __forceinline__ void stage_dict(const DecodeParams& p, uint4* s_dict, uint8_t* s_lens,
+                                                      int nthreads) {
+        if (!DSMEM) return;
+        if (PRESHIFT) {
+            const uint2* tab = reinterpret_cast<const uint2*>(p.dict.table);
+            for (int i = threadIdx.x; i < DICT_BYTES / 16; i += nthreads) {
+                const u32 b = (u32)i & 255u, r8 = (((u32)i >> 8) & 3u) * 8u;
+                u32 lo = b, hi = 0u;   // a literal byte
+                if (i < 1024) {
+                    const uint2 d = __ldg(tab + b);
+                    lo = d.x;
+                    hi = d.y;
+                }
+                s_dict[i] = make_uint4(lo << r8, __funnelshift_l(lo, hi, r8), __funnelshift_l(hi, 0u, r8), 0u);
+            }
+        } else {
+            const uint4* src = reinterpret_cast<const uint4*>((TOK8 || W == 16) ? p.dict.table : p.dict.planes);
+            for (int i = threadIdx.x; i < DICT_BYTES / 16; i += nthreads) s_dict[i] = __ldg(src + i);
+        }
+        const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
+        for (int i = threadIdx.x; i < LENS_BYTES / 16; i += nthreads) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
     }
 
     // Byte count of an escape-free lane whose K slots all lie inside the
@@ -979,13 +1020,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
     // packed codes: a scratch of PK_STRIDE words per lane after the warp areas
     u32* pk = PACKED ? reinterpret_cast<u32*>(areas + NW) + threadIdx.x * C::PK_STRIDE : nullptr;
     if (DSMEM) {
-        // FSST: the 8-byte entries as they are; OnPair read whole (W = 16): the
-        // 16-byte entries; OnPair split read (W = 8): the two planes (entry e's
-        // bytes 0..7 at low-plane word e, bytes 8..15 at high-plane word e)
-        const uint4* src = reinterpret_cast<const uint4*>((C::TOK8 || W == 16) ? p.dict.table : p.dict.planes);
-        for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
-        const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
-        for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
+        C::stage_dict(p, s_dict, s_lens, NW * 32);
         __syncthreads();
     }
     grid_wait();   // the tile scan's offsets (the dictionary staging above overlapped it)
@@ -1061,10 +1096,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fused_decode_kernel(const DecodePa
     uint8_t* s_lens = smem_raw + C::DICT_BYTES;
     WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
     if (DSMEM) {
-        const uint4* src = reinterpret_cast<const uint4*>((C::TOK8 || W == 16) ? p.dict.table : p.dict.planes);
-        for (int i = threadIdx.x; i < C::DICT_BYTES / 16; i += NW * 32) s_dict[i] = __ldg(src + i);
-        const uint4* lsrc = reinterpret_cast<const uint4*>(p.dict.lens);
-        for (int i = threadIdx.x; i < C::LENS_BYTES / 16; i += NW * 32) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
+        C::stage_dict(p, s_dict, s_lens, NW * 32);
         __syncthreads();
     }
     const uint8_t* lens = DSMEM ? s_lens : p.dict.lens;
