@@ -529,6 +529,34 @@ struct WarpCore {
         for (int i = threadIdx.x; i < LENS_BYTES / 16; i += nthreads) reinterpret_cast<uint4*>(s_lens)[i] = __ldg(lsrc + i);
     }
 
+    // The same staging by the bulk-copy engine where the staged layout is the
+    // stored one (no planes, no moved-up copies): thread 0 issues the two
+    // copies (cp.async.bulk, completion counted on one mbarrier) and every
+    // thread waits for them, bounded (a wait that gives up sets
+    // ERRB_TIMEOUT).  Falls back to the loads above for tables that are not
+    // 16-byte aligned.  Every thread of the block calls it; returns synchronised.
+    static constexpr bool BULK_STAGE = DSMEM && !PRESHIFT && (TOK8 || W == 16);
+    static __device__ __forceinline__ void stage_dict_bulk(const DecodeParams& p, uint4* s_dict, uint8_t* s_lens,
+                                                           u64* bar, int nthreads) {
+        const bool aligned =
+            ((reinterpret_cast<uintptr_t>(p.dict.table) | reinterpret_cast<uintptr_t>(p.dict.lens)) & 15u) == 0u;
+        if (!aligned) {
+            stage_dict(p, s_dict, s_lens, nthreads);
+            __syncthreads();
+            return;
+        }
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1u);
+            mbar_init_fence();
+            mbar_expect_tx(bar, (u32)(DICT_BYTES + LENS_BYTES));
+            bulk_g2s(s_dict, p.dict.table, (u32)DICT_BYTES, bar);
+            bulk_g2s(s_lens, p.dict.lens, (u32)LENS_BYTES, bar);
+            mbar_arrive(bar);
+        }
+        __syncthreads();   // the barrier is initialised before anyone waits on it
+        mbar_wait(bar, 0u, p.ws);
+    }
+
     // Byte count of an escape-free lane whose K slots all lie inside the
     // column, straight from its code words (constant bit positions): one
     // extract, one length load and one add per code; a code without a token
@@ -1019,7 +1047,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) warp_decode_kernel(const Decode
     WarpArea<K>* areas = reinterpret_cast<WarpArea<K>*>(smem_raw + C::DICT_BYTES + (DSMEM ? C::LENS_BYTES : 0));
     // packed codes: a scratch of PK_STRIDE words per lane after the warp areas
     u32* pk = PACKED ? reinterpret_cast<u32*>(areas + NW) + threadIdx.x * C::PK_STRIDE : nullptr;
-    if (DSMEM) {
+    __shared__ __align__(8) u64 s_bar;
+    if (C::BULK_STAGE) {
+        C::stage_dict_bulk(p, s_dict, s_lens, &s_bar, NW * 32);
+    } else if (DSMEM) {
         C::stage_dict(p, s_dict, s_lens, NW * 32);
         __syncthreads();
     }
