@@ -876,6 +876,76 @@ __global__ void __launch_bounds__(256, ReduceShape<CODEC, K>::MINB) reduce_kerne
     u32 err = 0;
     // rounds of U tiles; the next round's loads are in flight while this one computes
     constexpr int U = ReduceShape<CODEC, K>::U;
+    if constexpr (!C::FSST && !PACKED) {
+        // Escape-free codes in their own layout: tiles [t_lo, t_hi) lie wholly
+        // inside the column and the code buffer; their lanes load their code
+        // words at a fixed stride and sum their lengths straight from them
+        // (32-bit tile indices: fewer than 2^32 tiles).  Edge tiles take the
+        // general path.
+        constexpr u32 TB = C::TILE * C::WBITS / 8;   // code bytes of a tile
+        const u32 nt = (u32)x.n_tiles, W = (u32)warps;
+        const u64 buf_slots = p.codes_bytes * 8 / C::WBITS;
+        const u64 end = x.c_end < buf_slots ? x.c_end : buf_slots;
+        const u64 lo64 = (x.c_begin + C::TILE - 1) / C::TILE, hi64 = end / C::TILE;
+        const u32 t_lo = (u32)(lo64 - x.first_tile);
+        const u32 t_hi = hi64 > lo64 ? (u32)(hi64 - x.first_tile) : t_lo;
+        const uint8_t* base = p.codes + x.first_tile * (u64)TB + (u64)lane * C::LANE_BYTES;
+        auto load = [&](u32 t, u32 (&w)[C::LANE_WORDS]) {
+            if (C::LANE_BYTES % 16 == 0) {
+                const uint4* src = reinterpret_cast<const uint4*>(base + (u64)t * TB);
+#pragma unroll
+                for (int v = 0; v < C::LANE_WORDS / 4; ++v) {
+                    const uint4 a = __ldcs(src + v);
+                    w[4 * v] = a.x; w[4 * v + 1] = a.y; w[4 * v + 2] = a.z; w[4 * v + 3] = a.w;
+                }
+            } else {
+                const uint2* src = reinterpret_cast<const uint2*>(base + (u64)t * TB);
+#pragma unroll
+                for (int v = 0; v < C::LANE_WORDS / 2; ++v) {
+                    const uint2 a = __ldcs(src + v);
+                    w[2 * v] = a.x;
+                    w[2 * v + 1] = a.y;
+                }
+            }
+        };
+        u32 t = (u32)rblock * (blockDim.x / 32) + (threadIdx.x >> 5);
+        u32 wv[U][C::LANE_WORDS];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u32 tt = t + u * W;
+            if (tt >= t_lo && tt < t_hi) load(tt, wv[u]);
+        }
+        for (; t < nt; t += U * W) {
+            u32 nv[U][C::LANE_WORDS];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const u32 tt = t + (U + u) * W;
+                if (tt >= t_lo && tt < t_hi) load(tt, nv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const u32 tt = t + u * W;
+                if (tt >= nt) continue;
+                if (tt >= t_lo && tt < t_hi) {
+                    const u32 tot = __reduce_add_sync(0xffffffffu, C::lane_length_sum(wv[u], lens, err));
+                    if (lane == 31) agg[tt] = tot;
+                } else {
+                    u32 gw[C::LANE_WORDS];
+                    const bool fast = C::load_fast(p, C::lane_q0(x, tt), gw);
+                    typename C::R r;
+                    C::finish_load(p, x, C::lane_q0(x, tt), gw, fast, lens, r);
+                    const TElem e = C::tile_element(r, lane, err);
+                    if (lane == 31) agg[tt] = wt_pack<false>(e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int i = 0; i < C::LANE_WORDS; ++i) wv[u][i] = nv[u][i];
+        }
+        if (err) atomicOr(p.err_word, err);
+        return;
+    }
     u64 t0 = (u64)rblock * (blockDim.x / 32) + (threadIdx.x >> 5);
     u32 wv[U][C::LANE_WORDS];
     bool fast[U];
@@ -896,23 +966,10 @@ __global__ void __launch_bounds__(256, ReduceShape<CODEC, K>::MINB) reduce_kerne
         for (int u = 0; u < U; ++u) {
             const u64 t = t0 + u * warps;
             if (t < x.n_tiles) {
-                bool done = false;
-                if constexpr (!C::FSST && !PACKED) {
-                    // a whole tile of an escape-free column (all but the edge tiles)
-                    const u64 tile_start = (x.first_tile + t) * (u64)C::TILE;
-                    if (__all_sync(0xffffffffu, fast[u]) && tile_start >= x.c_begin &&
-                        tile_start + C::TILE <= x.c_end) {
-                        const u32 tot = __reduce_add_sync(0xffffffffu, C::lane_length_sum(wv[u], lens, err));
-                        if (lane == 31) agg[t] = tot;
-                        done = true;
-                    }
-                }
-                if (!done) {
-                    typename C::R r;
-                    C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r, s_pk + threadIdx.x * C::PK_STRIDE);
-                    const TElem e = C::tile_element(r, lane, err);
-                    if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
-                }
+                typename C::R r;
+                C::finish_load(p, x, C::lane_q0(x, t), wv[u], fast[u], lens, r, s_pk + threadIdx.x * C::PK_STRIDE);
+                const TElem e = C::tile_element(r, lane, err);
+                if (lane == 31) agg[t] = wt_pack<C::FSST>(e);
             }
         }
 #pragma unroll
