@@ -40,6 +40,13 @@ WORKLOADS = {
                             "FSST-12 with a 1,024-symbol table, codes cascaded: bit-packed at 10 bits and "
                             "unpacked inside the decode (fp_decode_packed); 16M lognormal strings (median 40 B)"),
 }
+# selective decode: name -> (column workload, rows selected, description)
+ROWS_WORKLOADS = {
+    "onpair12_10m_rows1m": ("onpair12_10m", 1_000_000,
+                            "1M distinct rows in random order out of the OnPair-12 10M-string column (fp_decode_rows: "
+                            "row scan, gather of the selected codes, warp-tile decode); the column stays resident"),
+}
+ROWS_METRIC = "decoded GB/s of the selected rows (selective decode, column resident in HBM)"
 # cascaded workloads: name -> (bits per stored code, dictionary entries)
 PACKED_WORKLOADS = {"fsst12_packed10_16m": (10, 1024)}
 # batched workloads: name -> (chunks, smallest and largest decoded chunk size, description)
@@ -531,6 +538,217 @@ class BatchInputs:
 
 def _align(x: int, a: int = 256) -> int:
     return (x + a - 1) // a * a
+
+
+def rows_selection(n_strings: int, n_rows: int, seed: int):
+    """n_rows distinct row ids of a column of n_strings, in random order."""
+    rng = np.random.default_rng((7, seed, n_rows))
+    return rng.permutation(n_strings)[:n_rows].astype(np.uint32)
+
+
+def rows_algorithmic_bytes(col, rows, total: int) -> int:
+    """Bytes a selective decode must move at least: the row ids, each
+    selected row's two code offsets and code bytes, the output and its
+    offsets, the dictionary once."""
+    co = col.code_offsets.astype(np.int64)
+    slots = int((co[rows.astype(np.int64) + 1] - co[rows]).sum())
+    code_bytes = (slots * synth.CODE_BITS[col.codec] + 7) // 8
+    d = col.dictionary
+    return 4 * rows.size + 8 * rows.size + code_bytes + total + 4 * (rows.size + 1) + \
+        d.n_entries * (synth.MAX_TOKEN[col.codec] + 1)
+
+
+def run_rows(args, rank, world, local_rank):
+    import torch
+    import paper_2609_15034_gb300 as fp
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    base, n_rows, desc = ROWS_WORKLOADS[args.workload]
+    codec, n, _ = WORKLOADS[base]
+    if args.n_strings:
+        n = args.n_strings
+    n_rows = min(n_rows, n)
+    col, _ = workload_column(base, rank, n)   # one independent replica column per rank
+    rows_h = rows_selection(n, n_rows, rank)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    d = fp.Dict(codec, col.dictionary.data, col.dictionary.offsets, sh)
+    codes = torch.from_numpy(col.stream).to(dev)
+    co = torch.from_numpy(col.code_offsets.view(np.int32)).to(dev)
+    rows = torch.from_numpy(rows_h.view(np.int32)).to(dev)
+    codes_bytes = codes.numel()
+    st, slots, total = fp.rows_size(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, rows.data_ptr(),
+                                    n_rows, sh)
+    if st != fp.OK:
+        raise RuntimeError(f"rows_size: {fp.STATUS_NAMES[st]} {fp.last_error()}")
+    out = torch.empty(total, dtype=torch.uint8, device=dev)
+    offs = torch.empty(n_rows + 1, dtype=torch.int32, device=dev)
+
+    def rows_call(rows_ptr, out_ptr, offs_ptr, stream_h):
+        fp.decode_rows(codec, d, codes.data_ptr(), codes_bytes, co.data_ptr(), n, rows_ptr, n_rows, slots, out_ptr,
+                       total, offs_ptr, stream_h)
+
+    def step():
+        rows_call(rows.data_ptr(), out.data_ptr(), offs.data_ptr(), sh)
+
+    step()
+    if fp.sync_status(sh) != fp.OK:
+        raise RuntimeError(fp.last_error())
+    gpu_id = str(local_rank)
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id)
+    t_end = time.time() + args.settle
+    while time.time() < t_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if fp.sync_status(sh) != fp.OK:
+        raise RuntimeError(fp.last_error())
+    total_ms, all_bytes = combine_ranks(dist, total_ms, float(total), dev)
+    value = all_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    avg_s = statistics.mean(launch_ms) * 1e-3
+    alg = rows_algorithmic_bytes(col, rows_h, total)
+    peak, peak_kind = load_peaks()
+    extra = {}
+    if rank == 0 and not args.quick:
+        # end to end: the row ids in from pinned host memory, the selected
+        # strings and their offsets back, every step (the column is resident,
+        # as in a column store that keeps it on the device)
+        h_rows = torch.from_numpy(rows_h.view(np.int32)).pin_memory()
+        h_out = torch.empty(total, dtype=torch.uint8).pin_memory()
+        h_offs = torch.empty(n_rows + 1, dtype=torch.int32).pin_memory()
+        d_rows = torch.empty_like(rows)
+
+        def e2e_step():
+            d_rows.copy_(h_rows, non_blocking=True)
+            rows_call(d_rows.data_ptr(), out.data_ptr(), offs.data_ptr(), sh)
+            h_out.copy_(out, non_blocking=True)
+            h_offs.copy_(offs, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_n = max(4, min(args.steps, 20))
+        a.record(stream)
+        for _ in range(e2e_n):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if fp.sync_status(sh) != fp.OK:
+            raise RuntimeError(fp.last_error())
+        if not torch.equal(h_out[:4096], out[:4096].cpu()) or not torch.equal(h_offs, offs.cpu()):
+            raise RuntimeError("end-to-end output mismatch")
+        e2e_s = a.elapsed_time(b) * 1e-3 / e2e_n
+        extra["e2e"] = {"value": round(total / e2e_s / 1e9, 3), "unit": "GB/s",
+                        "h2d_bytes_per_step": int(4 * n_rows), "d2h_bytes_per_step": int(total + 4 * (n_rows + 1)),
+                        "kind": "pinned host row ids in, selected bytes and offsets out, every step, one stream; "
+                                "the column stays resident"}
+        gbs, m, tb, dt = rows_cpu_rate(col, rows_h, args.cpu_seconds)
+        extra["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"first {m} of {n_rows} selected rows ({tb} decoded bytes), {dt:.1f} s"}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    var = fp.variant_for_dict(d, max(8, slots * synth.CODE_BITS[codec] // 8))
+    line = {
+        "metric": ROWS_METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc, "n_strings": n, "n_rows": n_rows,
+                   "selected_slots": int(slots), "decoded_bytes": int(total),
+                   "l2": "column and output larger than L2 (no flush needed)",
+                   "variant": dict(fp.variant_info(codec, var), index=var),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(alg / avg_s / 1e9, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(alg / avg_s / 1e9 / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": int(alg), "kernel_ms": round(avg_s * 1e3, 4)},
+        "clocks": clocks,
+        "gpu_launches": 7 * args.steps,   # row sums, their scan, row offsets, gather; reduce, tile scan, decode
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def rows_cpu_rate(col, rows, target_s: float):
+    """Time the oracle's selective decode (as it stands) on a bounded prefix
+    of the selection."""
+    import oracle
+    probe = min(rows.size, 20000)
+    args = (col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets)
+    t0 = time.perf_counter()
+    r = oracle.decode_rows(*args, rows[:probe])
+    dt = max(time.perf_counter() - t0, 1e-4)
+    m = int(min(rows.size, max(probe, probe * target_s / dt)))
+    t0 = time.perf_counter()
+    r = oracle.decode_rows(*args, rows[:m])
+    dt = time.perf_counter() - t0
+    return r.total / dt / 1e9, m, r.total, dt
+
+
+def run_rows_reference(args, rank, world):
+    if rank != 0:
+        return
+    base, n_rows, desc = ROWS_WORKLOADS[args.workload]
+    codec, n, _ = WORKLOADS[base]
+    if args.n_strings:
+        n = args.n_strings
+    n_rows = min(n_rows, n)
+    col, _ = workload_column(base, 0, n)
+    rows = rows_selection(n, n_rows, 0)
+    per_step = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
+    vals, last = [], None
+    for i in range(args.warmup + args.steps):
+        gbs, m, tb, dt = rows_cpu_rate(col, rows, per_step)
+        if i >= args.warmup:
+            vals.append(gbs)
+            last = (m, tb, dt)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": ROWS_METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(last[2] * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; stand-in for the paper's real columns)",
+        "config": {"workload": args.workload, "description": desc, "n_strings": n, "n_rows": n_rows},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {last[0]} of {n_rows} selected rows ({last[1]} decoded bytes) per step"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args, rank, world, local_rank):
@@ -1183,7 +1401,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="onpair12_10m",
-                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS))
+                    choices=sorted(WORKLOADS) + sorted(ROWS_WORKLOADS) + sorted(BATCH_WORKLOADS) +
+                    sorted(SERVE_WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed decoding before warm-up")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -1209,12 +1428,16 @@ def main():
     rank, world, local_rank = env_rank()
     batched = args.workload in BATCH_WORKLOADS
     served = args.workload in SERVE_WORKLOADS
+    rows = args.workload in ROWS_WORKLOADS
     if args.sidecar:
-        if batched or served:
+        if batched or served or rows:
             ap.error("--sidecar applies to the single-column workloads")
         args.quick = True
     if args.impl == "reference":
-        (run_batched_reference if batched else run_served_reference if served else run_reference)(args, rank, world)
+        (run_batched_reference if batched else run_served_reference if served else
+         run_rows_reference if rows else run_reference)(args, rank, world)
+    elif rows:
+        run_rows(args, rank, world, local_rank)
     elif served:
         if world > 1 and rank != 0:
             return   # one server per GPU is the product's unit; the served bench runs on rank 0
