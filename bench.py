@@ -113,6 +113,28 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def tuned_entry(codec: int, width: int, codes_bytes: int, sms: int):
+    """The committed tuning table's line for this GPU's SM count, codec, read
+    width and size class (floor(log2) of the buffer's code slots), if any:
+    the shape the default decode uses and its time when it was tuned."""
+    path = os.path.join(ROOT, "paper_2609_15034_gb300", "tuning", "gb300.txt")
+    slots = codes_bytes * 8 // synth.CODE_BITS[codec]
+    cls = max(slots, 1).bit_length() - 1
+    found = None
+    try:
+        with open(path) as f:
+            for ln in f:
+                if ln.startswith("#"):
+                    continue
+                v = ln.split()
+                if len(v) == 6 and [int(x) for x in v[:4]] == [sms, codec, width, cls]:
+                    found = {"variant": int(v[4]), "ms": float(v[5]), "size_class": cls,
+                             "table": "paper_2609_15034_gb300/tuning/gb300.txt"}
+    except OSError:
+        return None
+    return found
+
+
 def load_traffic(workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     a build whose single-column decode sources and flags equal this one's."""
@@ -463,6 +485,8 @@ def run_ours(args, rank, world, local_rank):
     else:
         var = fp.variant_for_dict(d, codes_bytes)
         vinfo = dict(fp.variant_info(codec, var), index=var, read_width=fp.variant_width(codec, var))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        vinfo["tuned"] = tuned_entry(codec, d.width, codes_bytes, sms)   # the table's line (None: built-in default)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,

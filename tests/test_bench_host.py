@@ -1,6 +1,7 @@
-"""Host logic of the selective-decode bench workload: the row selection is
-distinct, in range, in a seeded random order, and the algorithmic bytes
-count the selected rows' code slots exactly."""
+"""Host logic of bench.py: the selective-decode workload's row selection is
+distinct, in range and in a seeded random order, its algorithmic bytes
+count the selected rows' code slots exactly, and the bench line's tuned
+shape comes from the committed tuning table's line for the GPU."""
 import os
 import sys
 
@@ -30,3 +31,13 @@ def test_rows_algorithmic_bytes_counts_the_selected_slots():
     total = 1234
     want = 4 * 4 + 8 * 4 + (slots * 12 + 7) // 8 + total + 4 * 5 + col.dictionary.n_entries * 17
     assert bench.rows_algorithmic_bytes(col, rows, total) == want
+
+
+def test_tuned_entry_reads_the_committed_table():
+    path = os.path.join(ROOT, "paper_2609_15034_gb300", "tuning", "gb300.txt")
+    line = next(ln.split() for ln in open(path) if not ln.startswith("#"))
+    sms, codec, width, cls = (int(x) for x in line[:4])
+    codes_bytes = (1 << cls) * synth.CODE_BITS[codec] // 8
+    e = bench.tuned_entry(codec, width, codes_bytes, sms)
+    assert e is not None and e["size_class"] == cls
+    assert bench.tuned_entry(codec, width, codes_bytes, sms + 1) is None
