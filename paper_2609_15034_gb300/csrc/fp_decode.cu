@@ -150,7 +150,7 @@ cudaError_t launch_decode(int codec, const Variant& var, const DecodeParams& p_i
     const uint64_t tile = variant_tile(var);
     const uint64_t nb = (uint64_t)p.n_strings + 1;
     uint64_t ib = (nb + 256 * kIdxGroup - 1) / (256 * kIdxGroup);
-    if (ib > (uint64_t)sms * 8) ib = (uint64_t)sms * 8;
+    if (ib > (uint64_t)sms * 2) ib = (uint64_t)sms * 2;   // two index blocks per SM (an A/B: 8 per SM was 0.4 % slower)
     cudaError_t e;
     void* args[] = {(void*)&p};
     if (!var.warp_tiles) {
