@@ -1086,6 +1086,9 @@ __global__ void __launch_bounds__(256) tiles_scan_kernel(const DecodeParams p, c
         const u64 b = sh.ticket;
         if (b >= n_blocks) break;
         scan_block<FSST>(p, agg, ex, n, b, n_blocks, status, epoch, ws, sh);
+        // with a block per scan block the first tickets cover them all: no
+        // second ticket (one atomic round trip less at the end of the scan)
+        if ((u64)gridDim.x >= n_blocks) break;
     }
     finish_launch(ws, epoch);
 }
