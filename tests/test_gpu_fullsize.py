@@ -4,13 +4,17 @@ on the GPU and compared with the oracle's decode of the whole column (run on
 all host cores) byte for byte and offset for offset.  At these sizes the
 tile scan's look-back crosses dozens to hundreds of its 2,048-tile blocks.
 
-A second test decodes mid-size columns (several tile-scan blocks, hundreds
-of block-pipeline tiles) with every compiled variant, element by element."""
+The cascaded workload (16M strings, codes bit-packed at 10 bits) and the
+selective-decode workload (1M random rows of the 10M-string column) are
+compared whole in the same way.  A further test decodes mid-size columns
+(several tile-scan blocks, hundreds of block-pipeline tiles) with every
+compiled variant, element by element."""
 import os
 
 import numpy as np
 import pytest
 
+import bench
 import oracle
 import synth
 from gpu_util import DeviceColumn, oracle_decode
@@ -18,7 +22,7 @@ from gpu_util import DeviceColumn, oracle_decode
 pytestmark = pytest.mark.gpu
 
 FULL = [("onpair16_100k", synth.ONPAIR16, 100_000), ("onpair12_10m", synth.ONPAIR12, 10_000_000),
-        ("fsst8_16m", synth.FSST8, 16_000_000)]
+        ("fsst8_16m", synth.FSST8, 16_000_000), ("fsst12_16m", synth.FSST12, 16_000_000)]
 
 
 @pytest.fixture(scope="module")
@@ -28,7 +32,7 @@ def fp():
         pytest.skip("no CUDA device")
     import paper_2609_15034_gb300 as m
     yield m
-    for c in (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8):
+    for c in (synth.ONPAIR16, synth.ONPAIR12, synth.FSST8, synth.FSST12):
         m.variant_select(c, -1)
 
 
@@ -61,6 +65,67 @@ def test_full_size_every_element(fp, name, codec, n):
         raise AssertionError(f"{name}: first differing offset at {first_difference(offs_h[:n + 1], ref.offsets)}")
     if not np.array_equal(out_h[:total], ref.data):
         raise AssertionError(f"{name}: first differing byte at {first_difference(out_h[:total], ref.data)}")
+    d.free()
+
+
+def compare(fp, name, out, offs, total, n, ref):
+    out_h = out.cpu().numpy()
+    offs_h = offs.cpu().numpy().view(np.uint32)
+    assert np.all(out_h[total:] == 0xA5) and np.all(offs_h[n + 1:] == 0xFFFFFFFF), "write outside the buffers"
+    if not np.array_equal(offs_h[:n + 1], ref.offsets):
+        raise AssertionError(f"{name}: first differing offset at {first_difference(offs_h[:n + 1], ref.offsets)}")
+    if not np.array_equal(out_h[:total], ref.data):
+        raise AssertionError(f"{name}: first differing byte at {first_difference(out_h[:total], ref.data)}")
+
+
+def guarded(total, n):
+    import torch
+    out = torch.empty(total + 64, dtype=torch.uint8, device="cuda")
+    out[total:].fill_(0xA5)
+    offs = torch.empty(n + 1 + 16, dtype=torch.int32, device="cuda")
+    offs[n + 1:].fill_(-1)
+    return out, offs
+
+
+def test_full_size_cascaded_every_element(fp):
+    import torch
+    col, bits = bench.workload_column("fsst12_packed10_16m", 0)
+    n, codec = col.n_strings, col.codec
+    d = fp.Dict(codec, col.dictionary.data, col.dictionary.offsets)
+    codes = torch.from_numpy(col.stream).cuda()
+    co = torch.from_numpy(col.code_offsets.view(np.int32)).cuda()
+    st, total = fp.decoded_size_packed(codec, d, bits, codes.data_ptr(), codes.numel(), co.data_ptr(), n)
+    assert st == fp.OK
+    ref = oracle.decode_packed(codec, bits, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets)
+    assert ref.status == oracle.OK and total == ref.total
+    out, offs = guarded(total, n)
+    fp.decode_packed(codec, d, bits, codes.data_ptr(), codes.numel(), co.data_ptr(), n, out.data_ptr(), total,
+                     offs.data_ptr())
+    assert fp.sync_status() == fp.OK, fp.last_error()
+    compare(fp, "fsst12_packed10_16m", out, offs, total, n, ref)
+    d.free()
+
+
+def test_full_size_selected_rows_every_element(fp):
+    import torch
+    col = synth.column(synth.ONPAIR12, 0, 10_000_000)
+    rows_h = bench.rows_selection(col.n_strings, 1_000_000, 0)
+    d = fp.Dict(col.codec, col.dictionary.data, col.dictionary.offsets)
+    codes = torch.from_numpy(col.stream).cuda()
+    co = torch.from_numpy(col.code_offsets.view(np.int32)).cuda()
+    rows = torch.from_numpy(rows_h.view(np.int32)).cuda()
+    m = rows_h.size
+    st, slots, total = fp.rows_size(col.codec, d, codes.data_ptr(), codes.numel(), co.data_ptr(), col.n_strings,
+                                    rows.data_ptr(), m)
+    assert st == fp.OK
+    ref = oracle.decode_rows(col.codec, col.dictionary.data, col.dictionary.offsets, col.stream, col.code_offsets,
+                             rows_h)
+    assert ref.status == oracle.OK and total == ref.total
+    out, offs = guarded(total, m)
+    fp.decode_rows(col.codec, d, codes.data_ptr(), codes.numel(), co.data_ptr(), col.n_strings, rows.data_ptr(), m,
+                   slots, out.data_ptr(), total, offs.data_ptr())
+    assert fp.sync_status() == fp.OK, fp.last_error()
+    compare(fp, "onpair12_10m_rows1m", out, offs, total, m, ref)
     d.free()
 
 
